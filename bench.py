@@ -1,0 +1,354 @@
+"""Benchmark of the overlap-solve hot path on GB300.
+
+One step = one overlap solve D_N x = b to relative residual 1e-8 on the 16^4
+workload: seeded near-identity SU(3) links (eps = 0.5) smeared by 3 stout steps
+(rho_stout = 0.1), rho = 1, mu = 0.01, one Gaussian right-hand side. The headline
+arm is the mixed-precision solver (outer FP64 FGMRES, recursive inner FP32
+FGMRES with an FP32 sign function, inexact FP32 Wilson preconditioner at
+m0^def); the plain FP64 arm (FP64 everywhere, Wilson-preconditioned FGMRES) is
+timed beside it. Multi-GPU: replicas only (one independent solve per rank).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (16, 16, 16, 16)
+WORKLOAD = "16^4 overlap solve, 3-stout smeared eps=0.5 links, rho=1, mu=0.01, 1 Gaussian RHS, tol 1e-8"
+GAUGE_SEED, RHS_SEED = 1002, 2002
+TOL = 1e-8
+METRIC = "overlap solves/s at 1e-8 (mixed vs FP64 GPU); Dslash GB/s % HBM; p50/p99 latency"
+UNIT = "solves/s"
+KERNEL_SOURCES = ["paper_1410_7170_gb300/csrc/multishift.cu", "paper_1410_7170_gb300/csrc/wilson_site.cuh",
+                  "paper_1410_7170_gb300/csrc/common.cuh", "paper_1410_7170_gb300/csrc/reduce.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_from_profiles(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    if t.get("kernel_hash") != kernel_hash():
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(rank):
+    import synth
+    U = synth.gauge_field(DIMS, 0.5, GAUGE_SEED, stout_steps=3, stout_eps=0.1)
+    b = synth.rhs_gaussian(DIMS, RHS_SEED + rank)
+    return U, b
+
+
+def solver_params(ovl, mixed):
+    if mixed:
+        return ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32)
+    return ovl.params_default(precond=ovl.OVL_PREC_WILSON, precision=ovl.OVL_FP64)
+
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    import paper_1410_7170_gb300 as ovl
+    from paper_1410_7170_gb300 import build
+
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    U, b = make_inputs(rank)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    b_d = torch.from_numpy(b).to(dev)
+    x_d = torch.zeros_like(b_d)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed_solves(op, steps, warmup, prof=False):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                x_d.zero_()
+                op.ovl_solve(x_d, b_d, 1, TOL)
+        torch.cuda.synchronize()
+        if prof:
+            op.prof_enable(True)
+            op.prof_get(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stats = []
+        barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.zero_()
+                x_d.zero_()
+                ev[k][0].record(stream)
+                _, st = op.ovl_solve(x_d, b_d, 1, TOL)
+                ev[k][1].record(stream)
+                stats.append(st)
+        torch.cuda.synchronize()
+        barrier()
+        ms = sum(a.elapsed_time(bq) for a, bq in ev)
+        pr = op.prof_get(reset=True) if prof else None
+        return ms, stats, pr
+
+    dev_idx = torch.cuda.current_device()
+    # ---- mixed arm (headline)
+    op = ovl.Overlap(torch.from_numpy(U).to(dev), DIMS, 1.0, 0.01, solver_params(ovl, True),
+                     stream=stream.cuda_stream)
+    info = op.info()
+    with Clocks(dev_idx) as clk:
+        ms_mixed, st_mixed, prof = timed_solves(op, args.steps, args.warmup, prof=True)
+    clocks = clk.summary()
+    # accuracy of the headline result: true residual in FP64 through the library's own D_N
+    with torch.cuda.stream(stream):
+        r = torch.empty_like(b_d)
+        op.ovl_apply(r, x_d, 1e-12)
+        res_true = ((b_d - r).norm() / b_d.norm()).item()
+    # ---- e2e: host (pinned) buffers through the same C-ABI call, copies inside the timed region
+    b_h = torch.from_numpy(b).pin_memory()
+    x_h = torch.zeros_like(b_h).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x_h.zero_()
+        op.ovl_solve(x_h, b_h, 1, TOL)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    op.close()
+    # ---- plain FP64 arm
+    op64 = ovl.Overlap(torch.from_numpy(U).to(dev), DIMS, 1.0, 0.01, solver_params(ovl, False),
+                       stream=stream.cuda_stream)
+    fp64_steps = max(1, min(args.steps, 2))
+    ms_64, st_64, _ = timed_solves(op64, fp64_steps, 1)
+    op64.close()
+
+    # max over ranks
+    vals = torch.tensor([ms_mixed, e2e_s, ms_64], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_mixed, e2e_s, ms_64 = vals.tolist()
+    if rank != 0:
+        return None
+    pk, pk_kind = peaks()
+    # dominant kernel of the timed region
+    kern = {"ms_shifts": (prof["shifts_ms"], prof["shifts_launches"], prof["shifts_bytes"]),
+            "ms_stencil": (prof["stencil_ms"], prof["stencil_launches"], prof["stencil_bytes"])}
+    dom = max(kern, key=lambda k: kern[k][0])
+    t_ms, n_l, byt = kern[dom]
+    achieved = (byt / n_l) / (t_ms / n_l * 1e-3) / 1e9 if n_l and t_ms > 0 else None
+    per_launch_bytes = byt / n_l if n_l else None
+    V = int(np.prod(DIMS))
+    spinor_bytes = V * 12 * 16
+    out = {
+        "metric": METRIC,
+        "value": args.steps * world / (ms_mixed * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_mixed / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 outer / f32 inner",
+        "data": "synthetic (seeded SU(3) links exp(i 0.5 H), 3 stout steps; Gaussian RHS)",
+        "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "rho": 1.0, "mu": 0.01,
+                   "tol": TOL, "solver": "FGMRES(100) fp64 + inner FGMRES fp32 (Table 3) + Wilson FGMRES fp32",
+                   "n_poles": 20, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fp64_gpu": {"value": fp64_steps * world / (ms_64 * 1e-3), "unit": UNIT, "steps": fp64_steps,
+                     "warmup": 1, "outer_iters": st_64[-1]["outer_iters"],
+                     "ms_iters_fp64": st_64[-1]["ms_iters_fp64"]},
+        "mixed_stats": st_mixed[-1],
+        "true_rel_resid": res_true,
+        "spectral": info,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
+                     "peak_kind": pk_kind,
+                     "traffic": traffic_from_profiles(dom), "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "launches": n_l, "avg_launch_us": (t_ms / n_l * 1e3) if n_l else None,
+                     "other": {k: {"ms": v[0], "launches": v[1],
+                                   "GB/s": (v[2] / (v[0] * 1e-3) / 1e9) if v[0] > 0 else None}
+                               for k, v in kern.items()},
+                     "timing": "CUDA events recorded by the library around each launch in the timed region"},
+        "e2e": {"value": e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * spinor_bytes,
+                "d2h_bytes_per_step": spinor_bytes},
+        "gpu_launches": prof["launches"],
+        "clocks": clocks,
+    }
+    out["cpu_baseline"] = cpu_baseline(st_64[-1], budget_s=args.cpu_budget)
+    return out
+
+
+def cpu_baseline(st64=None, budget_s=15.0):
+    """The oracle on the host cores: plain CG iterations on (Q^2 + sigma) at the
+    workload size (its sign function runs one such CG per Zolotarev pole), timed on
+    a bounded sample and projected to solves/s with the Q^2 count of a solve."""
+    import numpy as np
+
+    from oracle import sparse
+    import synth
+    U = synth.gauge_field(DIMS, 0.5, GAUGE_SEED, stout_steps=3, stout_eps=0.1)
+    b = synth.rhs_gaussian(DIMS, RHS_SEED)
+    sparse.lib()
+    it = 2
+    while True:
+        t0 = time.perf_counter()
+        x, _ = sparse.cg_shift(b, U, DIMS, -1.0, 0.01, 1e-30, maxit=it)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 3 or it >= 512:
+            break
+        it *= 2
+    per_iter = dt / it
+    # one oracle solve: unpreconditioned GMRES, each D_N application = n_poles plain CGs; the
+    # multishift iteration count of the FP64 GPU solve bounds each pole's CG count from above
+    if st64 and st64.get("ms_iters_fp64"):
+        n_q2 = 20 * st64["ms_iters_fp64"]
+    else:
+        n_q2 = 20 * 3000
+    return {"value": 1.0 / (per_iter * n_q2), "unit": UNIT, "cores": sparse.threads(), "kind": "oracle",
+            "sample": "%d plain CG iterations on (Q^2+sigma) at 16^4 (%.2f s, %.3f s/iteration), projected "
+                      "with 20 poles x %d Q^2 applications per solve" % (it, dt, per_iter, n_q2 // 20)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from oracle import sparse  # noqa: F401
+    samples = []
+    for _ in range(args.warmup):
+        cpu_baseline(budget_s=2.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        samples.append(cpu_baseline(budget_s=args.cpu_budget))
+    elapsed = time.perf_counter() - t0
+    v = statistics.median(s["value"] for s in samples)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / max(1, args.steps) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS))},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": samples[-1]["cores"],
+                             "sample": samples[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "ours":
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, dist)
+    if out is not None:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

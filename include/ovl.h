@@ -1,0 +1,206 @@
+/* ovl.h — C ABI of the GB300 overlap-operator library (libovl.so).
+ *
+ * The library applies and inverts Neuberger's overlap operator
+ *
+ *     D_N = rho I + Gamma5 sign(Gamma5 D_W(m0_ker))          (Sec. 2, Eq. overlap_def)
+ *
+ * with the Wilson-Dirac kernel D_W of Eq. (Wilson-Dirac) (lattice spacing a = 1),
+ * kernel mass m0_ker = -rho_in and rho = (-mu/2 + m0_ker)/(mu/2 + m0_ker) (Sec. 5).
+ * sign(Q), Q = Gamma5 D_W, is evaluated with Zolotarev's optimal rational
+ * approximation on [lambda_min, lambda_max] of |Q| and a multishift conjugate
+ * gradient for the shifted systems (Q^2 + sigma_l) x_l = b. D_N psi = eta
+ * (Eq. linsys) is solved by restarted GMRES(m) or right-preconditioned
+ * FGMRES(m) in FP64 (Sec. 5.1), optionally with relaxation of the sign
+ * accuracy (Sec. 5.2) and a Wilson-Dirac preconditioner D_W(m0_prec)^{-1}
+ * (Sec. 3, Eq. default_m), applied inexactly (Sec. 5.1) or inside a nested
+ * FP32 inner FGMRES on D_N (Sec. 5.3).
+ *
+ * Field layout at the boundary (every vector argument):
+ *   lattice dims[4] = {L0, L1, L2, L3}, x0 = time; all L_mu even and >= 2;
+ *   lexicographic site index s = ((x0*L1 + x1)*L2 + x2)*L3 + x3;
+ *   spinor: V*12 complex doubles, interleaved (re, im), ordered [s][spin][colour]
+ *           (gamma matrices in the chiral basis gamma_0 = [[0,I],[I,0]],
+ *            gamma_k = [[0,-i sigma_k],[i sigma_k,0]], gamma_5 = diag(-1,-1,1,1));
+ *   several right-hand sides are n_rhs such vectors back to back;
+ *   gauge: V*4*9 complex doubles ordered [s][mu][row][col], U_mu(x) links x -> x+mu,
+ *          each an SU(3) matrix.
+ * Pointers may be device memory or host memory (pageable or pinned); the
+ * library detects which and copies host data in and out itself. The caller owns
+ * every buffer it passes; the library keeps no pointer to them after a call
+ * returns. A context owns all its device memory (gauge copies, workspace).
+ *
+ * Errors: every call returns an ovl_status; nothing aborts, traps or throws across
+ * the ABI. On error the output buffers are unspecified and ovl_last_error() gives
+ * a one-line reason. Calls on one context are ordered on the context's CUDA stream
+ * and return after the stream has finished the call's work; one context must not be
+ * used from two threads at once (different contexts may).
+ */
+#ifndef OVL_H
+#define OVL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ovl_ctx ovl_ctx;
+
+typedef enum {
+    OVL_OK = 0,
+    OVL_EINVAL = 1,       /* bad argument (size, pointer, non-SU(3) link, NaN input) */
+    OVL_ENOMEM = 2,       /* device memory / HBM budget exhausted */
+    OVL_ENOCONV = 3,      /* iteration cap reached before the tolerance */
+    OVL_EBREAKDOWN = 4,   /* Krylov breakdown (zero or non-finite scalar) */
+    OVL_ETIMEOUT = 5,     /* device-side iteration watchdog gave up */
+    OVL_ECUDA = 6         /* CUDA runtime error */
+} ovl_status;
+
+typedef enum {
+    OVL_FP64 = 0,         /* everything in FP64 */
+    OVL_MIXED_FP32 = 1,   /* inner (preconditioner) work in FP32, outer D_N in FP64 */
+    OVL_MIXED_HALF = 2    /* as MIXED_FP32, inner multishift vectors stored in FP16 */
+} ovl_precision;
+
+typedef enum {
+    OVL_PREC_NONE = 0,      /* GMRES(m), no preconditioner (Sec. 5.1 baseline) */
+    OVL_PREC_WILSON = 1,    /* FGMRES(m) right-preconditioned by an inexact D_W(m0_prec)^{-1} (Sec. 5.1) */
+    OVL_PREC_RECURSIVE = 2  /* FGMRES(m) preconditioned by an inner FP32 FGMRES on D_N, itself
+                               preconditioned by the inexact Wilson solve (Sec. 5.3) */
+} ovl_precond;
+
+/* Solver and approximation parameters. Defaults (ovl_params_default) are the
+ * paper's Table 2 / Table 3 values where the paper gives one. */
+typedef struct {
+    double tol_outer;       /* relative residual target ||b - D_N x|| / ||b|| (Table 2: 1e-8) */
+    int restart;            /* (F)GMRES restart length m (Table 2: 100) */
+    int relax;              /* 1: sign accuracy relaxed to tol_outer/||r_k||_rel * relax_factor (Sec. 5.2) */
+    double relax_factor;    /* Table 2: 1e-2 */
+    int n_poles;            /* Zolotarev poles n (1..64; default 20) */
+    double lambda_min;      /* spectral interval of |Q|; 0 = estimate by Lanczos at ovl_create */
+    double lambda_max;
+    double sign_tol;        /* accuracy of sign_apply inside ovl_apply/ovl_solve when relax = 0 */
+    int precond;            /* ovl_precond */
+    double m0_prec;         /* Wilson preconditioner mass; NaN = m0^def of Eq. (default_m) */
+    double eps_prec;        /* relative residual of the inexact Wilson solve (Table 2: 1e-1) */
+    double eps_inner;       /* inner FGMRES residual reduction (Table 3: 1e-2 with preconditioning) */
+    int restart_inner;      /* inner FGMRES restart length (Table 3: 100) */
+    int max_inner;          /* cap on inner FGMRES iterations per application */
+    int precision;          /* ovl_precision */
+    int antiperiodic;       /* 1: antiperiodic time boundary for the fermions, 0: periodic */
+    int max_iter;           /* cap on outer iterations */
+    int max_ms_iter;        /* cap on multishift CG iterations per sign application */
+    int sap_block[4];       /* Schwarz block extent (default 4,4,4,4); with a preconditioner each must be even and divide L_mu */
+    int sap_cycles;         /* Schwarz cycles per preconditioner application */
+    int sap_mr_iters;       /* minimal-residual steps per block solve */
+    int prec_restart;       /* restart length of the Wilson FGMRES in the inexact solve */
+    int prec_max_iter;      /* cap on Wilson FGMRES iterations per application */
+    int rhs_block;          /* right-hand sides per multi-RHS stencil launch (1..12) */
+    int use_graphs;         /* 1: capture multishift iterations in CUDA graphs */
+    int check_every;        /* multishift iterations between host convergence checks */
+    int stencil_tps;        /* threads per lattice site of the stencils: 0 = autotune, 1 or 4 = forced */
+} ovl_params;
+
+/* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
+typedef struct {
+    int outer_iters;        /* outer (F)GMRES iterations, summed over right-hand sides */
+    int inner_iters;        /* inner FGMRES iterations (recursive mode) */
+    long ms_iters_fp64;     /* multishift CG iterations in FP64 sign applications */
+    long ms_iters_low;      /* multishift CG iterations in FP32/FP16 sign applications */
+    long prec_iters;        /* Wilson FGMRES iterations inside the preconditioner */
+    double true_rel_resid;  /* max over RHS of ||b - D_N x|| / ||b||, recomputed in FP64 at exit */
+    double seconds;         /* wall time of the call */
+} ovl_stats;
+
+/* Fills *p with the defaults. Returns OVL_EINVAL if p is NULL. */
+ovl_status ovl_params_default(ovl_params *p);
+
+/* Creates a context for the lattice dims with kernel mass m0_ker = -rho_in and
+ * overlap mass mu (> 0): rho = (rho_in + mu/2)/(rho_in - mu/2) (Sec. 5 with m0_ker = -rho_in).
+ * gauge: V*4*9 complex doubles (see layout); copied and compressed to 12 reals per
+ * link; links that are not SU(3) to 1e-10 are rejected with OVL_EINVAL.
+ * p: NULL = defaults. cuda_stream: a cudaStream_t the context issues all work on
+ * (NULL = the context creates its own non-blocking stream).
+ * If lambda_min/lambda_max are 0 they are estimated here by Lanczos on Q^2.
+ * The Wilson preconditioner mass defaults to m0^def (Eq. default_m) with sigma_min
+ * from a fixed number of power iterations on D_W(0) (Sec. 5.1).
+ * On success *ctx is a new context; on error *ctx is NULL. */
+ovl_status ovl_create(ovl_ctx **ctx, const double *gauge, const int dims[4],
+                      double rho_in, double mu, const ovl_params *p, void *cuda_stream);
+
+/* out = D_W(m0) in, Eq. (Wilson-Dirac) (one spinor, any m0). */
+ovl_status wilson_apply(ovl_ctx *ctx, double *out, const double *in, double m0);
+
+/* x ~= D_W(m0)^{-1} b to relative residual tol: FGMRES(prec_restart) on D_W(m0), right-
+ * preconditioned by params.sap_cycles red-black Schwarz cycles over params.sap_block blocks
+ * (block solves by params.sap_mr_iters minimal-residual steps), at most params.prec_max_iter
+ * iterations; FP32 unless params.precision == OVL_FP64. This is the inexact Wilson solve the
+ * overlap solver uses as its preconditioner D_W(m0_prec)^{-1} (Sec. 3, Sec. 5.1). iters
+ * (nullable) receives the FGMRES iteration count. Needs even sap_block extents dividing dims. */
+ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, double m0, double tol, int *iters);
+
+/* Stencil variant chosen by the autotuner (threads per site, 1 or 4, for FP64 and FP32)
+ * and the measured ms per full-lattice stencil application of each variant
+ * (ms[0..3] = FP64 x1, FP64 x4, FP32 x1, FP32 x4; zeros when forced). Nullable outputs. */
+ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, float *ms);
+
+/* out ~= sign(Q) in, Q = Gamma5 D_W(m0_ker), to relative accuracy tol (>= 1e-14):
+ * Zolotarev rational approximation + FP64 multishift CG (Sec. 2, Eq. overlap_def). */
+ovl_status sign_apply(ovl_ctx *ctx, double *out, const double *in, double tol);
+
+/* out ~= D_N in = rho in + Gamma5 sign(Q) in (Eq. overlap_def), sign to accuracy tol. */
+ovl_status ovl_apply(ovl_ctx *ctx, double *out, const double *in, double tol);
+
+/* Solves D_N x = b (Eq. linsys) for n_rhs right-hand sides to relative residual tol
+ * (0 = params.tol_outer). x: n_rhs vectors; on entry the initial guess (zeros for none),
+ * on exit the solutions. The method is chosen by params.precond / params.precision.
+ * Returns OVL_ENOCONV if some right-hand side misses tol within max_iter (x then holds
+ * the best iterate). stats may be NULL. */
+ovl_status ovl_solve(ovl_ctx *ctx, double *x, const double *b, int n_rhs, double tol,
+                     ovl_stats *stats);
+
+/* Spectral data of the context: lambda_min, lambda_max of |Q|, Zolotarev error bound
+ * delta on that interval, rho, m0_ker, m0_prec, sigma_min estimate. Any pointer may be NULL. */
+ovl_status ovl_info(const ovl_ctx *ctx, double *lambda_min, double *lambda_max, double *delta,
+                    double *rho, double *m0_ker, double *m0_prec, double *sigma_min);
+
+/* Zolotarev coefficients on [k, 1] scaled by lambda_min (host computation, FP64):
+ * sign(x) ~= d0 x (1 + sum_l a[l] / (x^2 + c[l])), x in [1, 1/k]; n poles.
+ * Writes d0, a[n], c[n] and the uniform error bound delta. */
+ovl_status ovl_zolotarev(double k, int n, double *d0, double *a, double *c, double *delta);
+
+/* Instrumentation of the running library (used by the benchmark; not part of the
+ * paper's method). With profiling enabled, the multishift CG records CUDA events
+ * around its stencil and shift-update kernels in the same queued work (event nodes
+ * inside the captured graphs) and logs the shifts each iteration updated, so that
+ * kernel durations and algorithmic bytes (reals per site: Q p 96, residual update
+ * 144, shift update 72 + 48 per updated shift) are accumulated from the launches
+ * that do the work. Timings cost one event pair per kernel. */
+typedef struct {
+    long launches;          /* kernels launched by the library since the last reset (all contexts) */
+    double stencil_ms;      /* multishift stencil kernels (Q p and residual update): total time */
+    long stencil_launches;
+    double stencil_bytes;   /* their algorithmic bytes */
+    double shifts_ms;       /* multishift shift-update kernel */
+    long shifts_launches;
+    double shifts_bytes;
+    int valid;              /* 1 if every event timing could be read */
+} ovl_prof;
+
+/* on = 1 enables event timing (allocates a small history buffer), 0 disables it. */
+ovl_status ovl_prof_enable(ovl_ctx *ctx, int on);
+/* Reads the accumulated counters; reset = 1 zeroes them afterwards. */
+ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset);
+
+/* Destroys the context and frees its device memory. NULL is a no-op. */
+ovl_status ovl_destroy(ovl_ctx *ctx);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * ovl_create on this thread when ctx is NULL). Never NULL. */
+const char *ovl_last_error(const ovl_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OVL_H */

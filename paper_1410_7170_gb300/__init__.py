@@ -1,0 +1,264 @@
+"""Python binding of libovl.so, the GB300 overlap-operator library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library behind the C ABI declared in include/ovl.h. There is no CPU fallback;
+if the shared library has not been built, every call raises.
+
+Vectors are complex128 arrays [V][4][3] (or [n_rhs][V][4][3]) in lexicographic
+site order, as numpy arrays (host) or torch tensors (host or CUDA); gauge
+fields are complex128 [V][4][3][3].
+"""
+
+import ctypes
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libovl.so")
+
+OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ENOCONV, OVL_EBREAKDOWN, OVL_ETIMEOUT, OVL_ECUDA = range(7)
+OVL_FP64, OVL_MIXED_FP32, OVL_MIXED_HALF = range(3)
+OVL_PREC_NONE, OVL_PREC_WILSON, OVL_PREC_RECURSIVE = range(3)
+_STATUS = {0: "OVL_OK", 1: "OVL_EINVAL", 2: "OVL_ENOMEM", 3: "OVL_ENOCONV", 4: "OVL_EBREAKDOWN",
+           5: "OVL_ETIMEOUT", 6: "OVL_ECUDA"}
+
+
+class OvlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class ovl_params(ctypes.Structure):
+    _fields_ = [
+        ("tol_outer", ctypes.c_double), ("restart", ctypes.c_int), ("relax", ctypes.c_int),
+        ("relax_factor", ctypes.c_double), ("n_poles", ctypes.c_int), ("lambda_min", ctypes.c_double),
+        ("lambda_max", ctypes.c_double), ("sign_tol", ctypes.c_double), ("precond", ctypes.c_int),
+        ("m0_prec", ctypes.c_double), ("eps_prec", ctypes.c_double), ("eps_inner", ctypes.c_double),
+        ("restart_inner", ctypes.c_int), ("max_inner", ctypes.c_int), ("precision", ctypes.c_int),
+        ("antiperiodic", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_ms_iter", ctypes.c_int),
+        ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_iters", ctypes.c_int),
+        ("prec_restart", ctypes.c_int), ("prec_max_iter", ctypes.c_int), ("rhs_block", ctypes.c_int),
+        ("use_graphs", ctypes.c_int), ("check_every", ctypes.c_int), ("stencil_tps", ctypes.c_int),
+    ]
+
+
+class ovl_stats(ctypes.Structure):
+    _fields_ = [
+        ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("ms_iters_fp64", ctypes.c_long),
+        ("ms_iters_low", ctypes.c_long), ("prec_iters", ctypes.c_long), ("true_rel_resid", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ovl_prof(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_long), ("stencil_ms", ctypes.c_double), ("stencil_launches", ctypes.c_long),
+        ("stencil_bytes", ctypes.c_double), ("shifts_ms", ctypes.c_double), ("shifts_launches", ctypes.c_long),
+        ("shifts_bytes", ctypes.c_double), ("valid", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
+           "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
+           "wilson_solve", "ovl_tuning"]
+
+_lib = None
+
+
+def lib():
+    """Loads libovl.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libovl.so not built (%s); run paper_1410_7170_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, I_, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.ovl_params_default.argtypes = [ctypes.POINTER(ovl_params)]
+        L.ovl_create.argtypes = [ctypes.POINTER(P), P, P, D, D, ctypes.POINTER(ovl_params), P]
+        L.wilson_apply.argtypes = [P, P, P, D]
+        L.sign_apply.argtypes = [P, P, P, D]
+        L.ovl_apply.argtypes = [P, P, P, D]
+        L.ovl_solve.argtypes = [P, P, P, I_, D, ctypes.POINTER(ovl_stats)]
+        L.ovl_info.argtypes = [P] + [ctypes.POINTER(D)] * 7
+        L.ovl_zolotarev.argtypes = [D, I_, ctypes.POINTER(D), P, P, ctypes.POINTER(D)]
+        L.ovl_destroy.argtypes = [P]
+        L.ovl_last_error.argtypes = [P]
+        L.ovl_last_error.restype = ctypes.c_char_p
+        L.ovl_prof_enable.argtypes = [P, I_]
+        L.ovl_prof_get.argtypes = [P, ctypes.POINTER(ovl_prof), I_]
+        L.wilson_solve.argtypes = [P, P, P, D, D, ctypes.POINTER(I_)]
+        L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
+        for name in EXPORTS:
+            if name not in ("ovl_last_error",):
+                getattr(L, name).restype = I_
+        _lib = L
+    return _lib
+
+
+def _ptr(a, writable=False):
+    """Data pointer of a contiguous numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if hasattr(a, "__array_interface__"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if writable and not a.flags["WRITEABLE"]:
+            raise ValueError("array must be writable")
+        return ctypes.c_void_p(a.__array_interface__["data"][0])
+    raise TypeError("expected a numpy array or torch tensor")
+
+
+def _check(st, ctx=None):
+    if st != OVL_OK:
+        raise OvlError(st, lib().ovl_last_error(ctx).decode())
+
+
+def params_default(**kw):
+    p = ovl_params()
+    _check(lib().ovl_params_default(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k == "sap_block":
+            for m in range(4):
+                p.sap_block[m] = int(v[m])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def ovl_zolotarev(k, n):
+    """(d0, a[n], c[n], delta) of the library's host Zolotarev computation."""
+    import numpy as np
+    a = np.zeros(n)
+    c = np.zeros(n)
+    d0 = ctypes.c_double()
+    delta = ctypes.c_double()
+    _check(lib().ovl_zolotarev(float(k), int(n), ctypes.byref(d0), _ptr(a), _ptr(c), ctypes.byref(delta)))
+    return d0.value, a, c, delta.value
+
+
+def ovl_create(gauge, dims, rho, mu, params=None, stream=None):
+    import numpy as np
+    ctx = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    st = lib().ovl_create(ctypes.byref(ctx), _ptr(gauge), ctypes.cast(d, ctypes.c_void_p), float(rho),
+                          float(mu), ctypes.byref(params) if params is not None else None,
+                          ctypes.c_void_p(stream) if stream else None)
+    _check(st, None)
+    return ctx
+
+
+def ovl_destroy(ctx):
+    if ctx:
+        _check(lib().ovl_destroy(ctx))
+
+
+def wilson_apply(ctx, out, inp, m0):
+    _check(lib().wilson_apply(ctx, _ptr(out, True), _ptr(inp), float(m0)), ctx)
+    return out
+
+
+def sign_apply(ctx, out, inp, tol):
+    _check(lib().sign_apply(ctx, _ptr(out, True), _ptr(inp), float(tol)), ctx)
+    return out
+
+
+def ovl_apply(ctx, out, inp, tol):
+    _check(lib().ovl_apply(ctx, _ptr(out, True), _ptr(inp), float(tol)), ctx)
+    return out
+
+
+def ovl_solve(ctx, x, b, n_rhs=1, tol=0.0, check=True):
+    """Solves D_N x = b in place on x; returns (status, stats dict)."""
+    s = ovl_stats()
+    st = lib().ovl_solve(ctx, _ptr(x, True), _ptr(b), int(n_rhs), float(tol), ctypes.byref(s))
+    if check and st != OVL_OK:
+        _check(st, ctx)
+    return st, s.as_dict()
+
+
+def wilson_solve(ctx, x, b, m0, tol):
+    """x ~ D_W(m0)^{-1} b (SAP-preconditioned FGMRES); returns the iteration count."""
+    it = ctypes.c_int()
+    _check(lib().wilson_solve(ctx, _ptr(x, True), _ptr(b), float(m0), float(tol), ctypes.byref(it)), ctx)
+    return it.value
+
+
+def ovl_tuning(ctx):
+    import numpy as np
+    a, b = ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(4, dtype=np.float32)
+    _check(lib().ovl_tuning(ctx, ctypes.byref(a), ctypes.byref(b), _ptr(ms)), ctx)
+    return {"tps64": a.value, "tps32": b.value, "ms": ms.tolist()}
+
+
+def ovl_info(ctx):
+    vals = [ctypes.c_double() for _ in range(7)]
+    _check(lib().ovl_info(ctx, *[ctypes.byref(v) for v in vals]), ctx)
+    keys = ["lambda_min", "lambda_max", "delta", "rho", "m0_ker", "m0_prec", "sigma_min"]
+    return {k: v.value for k, v in zip(keys, vals)}
+
+
+def ovl_prof_enable(ctx, on=True):
+    _check(lib().ovl_prof_enable(ctx, int(bool(on))), ctx)
+
+
+def ovl_prof_get(ctx, reset=False):
+    out = ovl_prof()
+    _check(lib().ovl_prof_get(ctx, ctypes.byref(out), int(bool(reset))), ctx)
+    return out.as_dict()
+
+
+class Overlap:
+    """Owns one library context (ovl_create ... ovl_destroy)."""
+
+    def __init__(self, gauge, dims, rho, mu, params=None, stream=None):
+        self.dims = tuple(int(x) for x in dims)
+        self.V = int(math.prod(self.dims))
+        self.ctx = ovl_create(gauge, self.dims, rho, mu, params, stream)
+
+    def close(self):
+        if self.ctx:
+            ovl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def wilson_apply(self, out, inp, m0):
+        return wilson_apply(self.ctx, out, inp, m0)
+
+    def sign_apply(self, out, inp, tol):
+        return sign_apply(self.ctx, out, inp, tol)
+
+    def ovl_apply(self, out, inp, tol):
+        return ovl_apply(self.ctx, out, inp, tol)
+
+    def ovl_solve(self, x, b, n_rhs=1, tol=0.0, check=True):
+        return ovl_solve(self.ctx, x, b, n_rhs, tol, check)
+
+    def info(self):
+        return ovl_info(self.ctx)
+
+    def wilson_solve(self, x, b, m0, tol):
+        return wilson_solve(self.ctx, x, b, m0, tol)
+
+    def tuning(self):
+        return ovl_tuning(self.ctx)
+
+    def prof_enable(self, on=True):
+        ovl_prof_enable(self.ctx, on)
+
+    def prof_get(self, reset=False):
+        return ovl_prof_get(self.ctx, reset)

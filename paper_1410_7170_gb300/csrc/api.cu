@@ -1,0 +1,867 @@
+// C-ABI entry points and the host-side control of the solvers.
+//
+//   ovl_create   gauge upload/compression, spectral bounds of |Q| by Lanczos on Q^2,
+//                Zolotarev coefficients, sigma_min by power iteration (Sec. 5.1)
+//   wilson_apply D_W(m0) (Eq. Wilson-Dirac)
+//   sign_apply   sign(Q) by Zolotarev + multishift CG
+//   ovl_apply    D_N = rho I + Gamma5 sign(Q) (Eq. overlap_def)
+//   ovl_solve    GMRES(m) / FGMRES(m) on D_N psi = eta (Eq. linsys, Sec. 5.1-5.3)
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <complex>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../../include/ovl.h"
+#include "internal.h"
+#include "solver.h"
+
+using namespace ovl;
+
+static thread_local std::string g_create_error;
+
+// ------------------------------------------------------------------ defaults
+extern "C" ovl_status ovl_params_default(ovl_params *p) {
+    if (!p) return OVL_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->tol_outer = 1e-8;       // Table 2
+    p->restart = 100;          // Table 2
+    p->relax = 1;              // Sec. 5.2
+    p->relax_factor = 1e-2;    // Table 2
+    p->n_poles = 20;
+    p->lambda_min = 0.0;
+    p->lambda_max = 0.0;
+    p->sign_tol = 1e-12;
+    p->precond = OVL_PREC_NONE;
+    p->m0_prec = NAN;          // m0^def (Eq. default_m)
+    p->eps_prec = 1e-1;        // Table 2
+    p->eps_inner = 1e-2;       // Table 3 (with preconditioning)
+    p->restart_inner = 100;    // Table 3
+    p->max_inner = 200;
+    p->precision = OVL_FP64;
+    p->antiperiodic = 1;
+    p->max_iter = 5000;
+    p->max_ms_iter = 20000;
+    for (int m = 0; m < 4; m++) p->sap_block[m] = 4;
+    p->sap_cycles = 2;
+    p->sap_mr_iters = 4;
+    p->prec_restart = 16;
+    p->prec_max_iter = 64;
+    p->rhs_block = 1;
+    p->use_graphs = 1;
+    p->check_every = 8;
+    p->stencil_tps = 0;
+    return OVL_OK;
+}
+
+static ovl_status validate_params(const ovl_params &p, const int L[4], std::string &err) {
+    char buf[256];
+    if (!(p.tol_outer > 0 && p.tol_outer < 1)) { err = "tol_outer must be in (0,1)"; return OVL_EINVAL; }
+    if (p.restart < 2 || p.restart > 120) { err = "restart must be in [2,120]"; return OVL_EINVAL; }
+    if (p.restart_inner < 2 || p.restart_inner > 120) { err = "restart_inner must be in [2,120]"; return OVL_EINVAL; }
+    if (p.prec_restart < 2 || p.prec_restart > 120) { err = "prec_restart must be in [2,120]"; return OVL_EINVAL; }
+    if (p.n_poles < 1 || p.n_poles > kMaxPoles) {
+        snprintf(buf, sizeof buf, "n_poles must be in [1,%d]", kMaxPoles);
+        err = buf;
+        return OVL_EINVAL;
+    }
+    if (p.lambda_min < 0 || p.lambda_max < 0 || (p.lambda_min > 0 && !(p.lambda_max > p.lambda_min))) {
+        err = "need 0 < lambda_min < lambda_max (or both 0 to estimate)";
+        return OVL_EINVAL;
+    }
+    if (p.precond < 0 || p.precond > 2) { err = "precond must be 0, 1 or 2"; return OVL_EINVAL; }
+    if (p.precision < 0 || p.precision > 2) { err = "precision must be 0, 1 or 2"; return OVL_EINVAL; }
+    if (p.max_iter < 1 || p.max_ms_iter < 1 || p.check_every < 1) { err = "iteration caps must be >= 1"; return OVL_EINVAL; }
+    if (p.rhs_block < 1 || p.rhs_block > 12) { err = "rhs_block must be in [1,12]"; return OVL_EINVAL; }
+    if (p.stencil_tps != 0 && p.stencil_tps != 1 && p.stencil_tps != 4) { err = "stencil_tps must be 0, 1 or 4"; return OVL_EINVAL; }
+    for (int m = 0; m < 4 && p.precond != OVL_PREC_NONE; m++) {
+        if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m]) {
+            err = "sap_block must be even and divide the lattice extent";
+            return OVL_EINVAL;
+        }
+    }
+    if (p.precond != OVL_PREC_NONE) {
+        const int nb = p.sap_block[0] * p.sap_block[1] * p.sap_block[2] * p.sap_block[3];
+        if (nb > 256) { err = "sap_block volume must be <= 256 sites"; return OVL_EINVAL; }
+        if (p.sap_cycles < 1 || p.sap_mr_iters < 1) { err = "sap_cycles, sap_mr_iters must be >= 1"; return OVL_EINVAL; }
+    }
+    return OVL_OK;
+}
+
+// ------------------------------------------------------------------ helpers
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define CK(expr)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            c->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #expr; \
+            return OVL_ECUDA;                                                      \
+        }                                                                          \
+    } while (0)
+
+#define ST(expr)                          \
+    do {                                  \
+        ovl_status s_ = (expr);           \
+        if (s_ != OVL_OK) return s_;      \
+    } while (0)
+
+ovl_status Ctx::alloc(void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        err = "device allocation of " + std::to_string(bytes) + " bytes failed";
+        *p = nullptr;
+        return OVL_ENOMEM;
+    }
+    allocs.push_back(*p);
+    bytes_held += bytes;
+    return OVL_OK;
+}
+
+Ctx::~Ctx() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto &gr : graphs)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    for (int w = 0; w < 2; w++)
+        if (ev_ready[w])
+            for (int k = 0; k < kMaxChunk * 4; k++) cudaEventDestroy(ev[w][k]);
+    for (void *p : allocs) cudaFree(p);
+    if (h_pinned) cudaFreeHost(h_pinned);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+ovl_status Ctx::sync() {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        err = std::string("CUDA: ") + cudaGetErrorString(e);
+        return OVL_ECUDA;
+    }
+    return OVL_OK;
+}
+
+// Device scalars -> host (pinned), synchronising the stream.
+ovl_status Ctx::fetch(const double *d, int n, double *h) {
+    Ctx *c = this;
+    CK(cudaMemcpyAsync(h_scal, d, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    ST(sync());
+    memcpy(h, h_scal, n * sizeof(double));
+    return OVL_OK;
+}
+
+ovl_status Ctx::norm2_d(const double *x, double *out) {
+    Ctx *c = this;
+    CK(dev_norm2(x, n64, d_scal, rs, stream));
+    return fetch(d_scal, 1, out);
+}
+ovl_status Ctx::norm2_f(const float *x, double *out) {
+    Ctx *c = this;
+    CK(dev_norm2_f(x, n64, d_scal, rs, stream));
+    return fetch(d_scal, 1, out);
+}
+
+// Copy a boundary vector (host or device, lexicographic) into an internal FP64 eo vector.
+ovl_status Ctx::import_vec(const double *src, double2 *dst) {
+    Ctx *c = this;
+    const double *lex = src;
+    if (!is_device_ptr(src)) {
+        CK(cudaMemcpyAsync(io_lex, src, n64 * sizeof(double), cudaMemcpyHostToDevice, stream));
+        lex = io_lex;
+    }
+    CK(pack_spinor_f64(g, dst, lex, stream));
+    CK(cudaMemsetAsync(d_flag, 0, sizeof(int), stream));
+    CK(dev_nonfinite((const double *)dst, n64, d_flag, stream));
+    int h = 0;
+    CK(cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    ST(sync());
+    h = *h_flag;
+    if (h) {
+        err = "input vector holds NaN or Inf";
+        return OVL_EINVAL;
+    }
+    return OVL_OK;
+}
+
+ovl_status Ctx::export_vec(const double2 *src, double *dst) {
+    Ctx *c = this;
+    if (is_device_ptr(dst)) {
+        CK(unpack_spinor_f64(g, dst, src, stream));
+        return sync();
+    }
+    CK(unpack_spinor_f64(g, io_lex, src, stream));
+    CK(cudaMemcpyAsync(dst, io_lex, n64 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    return sync();
+}
+
+// ------------------------------------------------------------------ multishift sign
+// Fills the multishift state for tolerance tol and uploads it.
+ovl_status Ctx::ms_setup(MsState *d_state, double tol) {
+    Ctx *c = this;
+    MsState &s = *h_ms;
+    memset(&s, 0, sizeof(MsState));
+    s.n = npole;
+    s.tol = tol;
+    s.alpha_prev = 1.0;
+    s.beta_prev = 0.0;
+    for (int l = 0; l < npole; l++) {
+        s.sigma[l] = lam_min * lam_min * zc[l];
+        s.w[l] = za[l] * lam_min * lam_min;
+        // ||(d0/lmin) Q w_l (Q^2+sigma_l)^{-1} r_l|| <= d0 |a_l| ||r_l|| / (2 sqrt(c_l)); summed over l
+        s.crit[l] = npole * zd0 * fabs(za[l]) / (2.0 * sqrt(zc[l]));
+        s.zeta[l] = 1.0;
+        s.zeta_prev[l] = 1.0;
+        s.active[l] = 1;
+    }
+    s.hist = prof ? d_hist : nullptr;
+    s.hist_cap = prof ? hist_cap : 0;
+    CK(cudaMemcpyAsync(d_state, h_ms, sizeof(MsState), cudaMemcpyHostToDevice, stream));
+    return OVL_OK;
+}
+
+// Polls the device state every check_every iterations; graphs replay the chunk.
+// With instrumentation on, event records around the first three kernels of every
+// iteration are part of the queued work (event record nodes inside graphs) and the
+// device logs how many shifts each iteration updated, so per-kernel durations and
+// algorithmic bytes come from the same launches that do the work.
+template <typename Iter>
+ovl_status Ctx::ms_run(MsState *d_state, int which, Iter iter_fn, int *iters_out) {
+    Ctx *c = this;
+    const int chunk = std::min(p.check_every, kMaxChunk);
+    const double rbytes = which == 0 ? 8.0 : 4.0;
+    int done_iters = 0, iter_before = 0;
+    GraphSlot &gs = graphs[which];
+    if (prof && !ev_ready[which]) {
+        for (int k = 0; k < kMaxChunk * 4; k++) CK(cudaEventCreate(&ev[which][k]));
+        ev_ready[which] = true;
+    }
+    if (gs.exec && (gs.chunk != chunk || gs.prof != prof)) {
+        cudaGraphExecDestroy(gs.exec);
+        gs.exec = nullptr;
+    }
+    while (true) {
+        if (p.use_graphs) {
+            if (!gs.exec) {
+                cudaGraph_t graph;
+                set_launch_counting(false);
+                CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaSuccess;
+                for (int k = 0; k < chunk && ce == cudaSuccess; k++)
+                    ce = iter_fn(prof ? &ev[which][4 * k] : nullptr, cudaEventRecordExternal);
+                cudaError_t ee = cudaStreamEndCapture(stream, &graph);
+                set_launch_counting(true);
+                CK(ce);
+                CK(ee);
+                cudaError_t ie = cudaGraphInstantiate(&gs.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                CK(ie);
+                gs.chunk = chunk;
+                gs.prof = prof;
+            }
+            CK(cudaGraphLaunch(gs.exec, stream));
+            count_launches(4L * chunk);
+        } else {
+            for (int k = 0; k < chunk; k++) CK(iter_fn(prof ? &ev[which][4 * k] : nullptr, 0u));
+        }
+        done_iters += chunk;
+        CK(cudaMemcpyAsync(h_ms_small, d_state, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream));
+        if (prof) CK(cudaMemcpyAsync(h_hist, d_hist + iter_before, chunk * sizeof(int), cudaMemcpyDeviceToHost,
+                                     stream));
+        ST(sync());
+        const int iter = h_ms_small[1], done = h_ms_small[2], status = h_ms_small[3];
+        if (prof) {
+            const int ran = std::min(chunk, iter - iter_before);
+            const double V = (double)g.V;
+            for (int k = 0; k < ran; k++) {
+                float a = 0, b = 0, d = 0;
+                if (cudaEventElapsedTime(&a, ev[which][4 * k], ev[which][4 * k + 1]) != cudaSuccess ||
+                    cudaEventElapsedTime(&b, ev[which][4 * k + 1], ev[which][4 * k + 2]) != cudaSuccess ||
+                    cudaEventElapsedTime(&d, ev[which][4 * k + 2], ev[which][4 * k + 3]) != cudaSuccess) {
+                    cudaGetLastError();
+                    pacc.valid = false;
+                    continue;
+                }
+                pacc.q_ms += a; pacc.r_ms += b; pacc.s_ms += d;
+                pacc.q_n++; pacc.r_n++; pacc.s_n++;
+                // algorithmic reals per site: Q p: p, 4 links x 12, t; residual: t, links, p, r in/out;
+                // shifts: r, y in/out, each updated p_l in/out
+                pacc.q_bytes += 96.0 * V * rbytes;
+                pacc.r_bytes += 144.0 * V * rbytes;
+                pacc.s_bytes += (72.0 + 48.0 * h_hist[k]) * V * rbytes;
+            }
+        }
+        iter_before = iter;
+        if (status) {
+            err = "multishift CG breakdown (non-finite or non-positive scalar)";
+            return OVL_EBREAKDOWN;
+        }
+        if (done) {
+            *iters_out = iter;
+            return OVL_OK;
+        }
+        if (iter >= p.max_ms_iter || done_iters > p.max_ms_iter + chunk) {
+            *iters_out = iter;
+            err = "multishift CG reached max_ms_iter";
+            return OVL_ENOCONV;
+        }
+    }
+}
+
+// y = b + sum_l w_l (Q^2+sigma_l)^{-1} b in FP64; then
+//   mode 0: out = (d0/lmin) gamma5 D_W y = sign(Q) b
+//   mode 1: out = rho b + (d0/lmin) D_W y   = D_N b
+ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
+    Ctx *c = this;
+    ST(ensure_ms64());
+    ST(ms_setup(ms64_state, tol));
+    CK(ms_init_f64(g, npole, ms64_state, ms64, b, rs, stream));
+    int iters = 0;
+    auto fn = [&](cudaEvent_t *e, unsigned f) { return ms_iter_f64(g, U64, m0_ker, ms64_state, ms64, rs, stream, e, f); };
+    ST(ms_run(ms64_state, 0, fn, &iters));
+    stat_ms64 += iters;
+    const double sc = zd0 / lam_min;
+    if (mode == 0) CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 1, sc, nullptr, 0.0, stream));
+    else CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 0, sc, b, rho, stream));
+    return OVL_OK;
+}
+
+// FP32 version for the inner (low-accuracy) D_N: b, out FP32 eo spinors.
+ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
+    Ctx *c = this;
+    ST(ensure_ms32());
+    ST(ms_setup(ms32_state, tol));
+    CK(ms_init_f32(g, npole, ms32_state, ms32, b, rs, stream));
+    int iters = 0;
+    auto fn = [&](cudaEvent_t *e, unsigned f) {
+        return ms_iter_f32(g, U32, (float)m0_ker, ms32_state, ms32, rs, stream, e, f);
+    };
+    ST(ms_run(ms32_state, 1, fn, &iters));
+    stat_ms32 += iters;
+    const float sc = (float)(zd0 / lam_min);
+    if (mode == 0) CK(wilson_f32(g, U32, ms32.y, out, (float)m0_ker, 1, sc, nullptr, 0.f, stream));
+    else CK(wilson_f32(g, U32, ms32.y, out, (float)m0_ker, 0, sc, b, (float)rho, stream));
+    return OVL_OK;
+}
+
+ovl_status Ctx::ensure_ms64() {
+    if (ms64.p) return OVL_OK;
+    const long words = (long)g.V * 12;   // double2 per vector
+    void *buf;
+    ST(alloc(&buf, (size_t)words * sizeof(double2) * (npole + 3)));
+    double2 *b2 = (double2 *)buf;
+    ms64.r = b2;
+    ms64.t = b2 + words;
+    ms64.y = b2 + 2 * words;
+    ms64.p = b2 + 3 * words;
+    ms64.stride = words;
+    return OVL_OK;
+}
+ovl_status Ctx::ensure_ms32() {
+    if (ms32.p) return OVL_OK;
+    const long words = (long)g.V * 6;    // float4 per vector
+    void *buf;
+    ST(alloc(&buf, (size_t)words * sizeof(float4) * (npole + 3)));
+    float4 *b4 = (float4 *)buf;
+    ms32.r = b4;
+    ms32.t = b4 + words;
+    ms32.y = b4 + 2 * words;
+    ms32.p = b4 + 3 * words;
+    ms32.stride = words;
+    return OVL_OK;
+}
+
+// ------------------------------------------------------------------ spectral estimates
+// Tridiagonal eigenvalue bounds by Sturm-sequence bisection.
+static int sturm_count(const std::vector<double> &a, const std::vector<double> &b, int m, double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; i++) {
+        const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+        d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0) cnt++;
+    }
+    return cnt;
+}
+static double tridiag_eig(const std::vector<double> &a, const std::vector<double> &b, int m, int k) {
+    // k-th smallest eigenvalue (0-based) of the m x m symmetric tridiagonal (a, b)
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; i++) {
+        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(fabs(lo), fabs(hi)); it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(a, b, m, mid) > k) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Lanczos on Q^2 in FP32 (no re-orthogonalisation: extremal Ritz values converge
+// first and spurious copies do not move them).
+ovl_status Ctx::lanczos_bounds(double *lmin, double *lmax) {
+    Ctx *c = this;
+    const long nf = n64;   // floats per FP32 vector
+    float *v0, *v1, *w, *tt;
+    void *buf;
+    ST(alloc(&buf, (size_t)nf * sizeof(float) * 4));
+    v0 = (float *)buf;
+    v1 = v0 + nf;
+    w = v1 + nf;
+    tt = w + nf;
+    // deterministic start vector
+    std::vector<float> h(nf);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (long i = 0; i < nf; i++) {
+        st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+        h[i] = (float)((double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    }
+    CK(cudaMemcpyAsync(v1, h.data(), nf * sizeof(float), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemsetAsync(v0, 0, nf * sizeof(float), stream));
+    double nn;
+    ST(norm2_f(v1, &nn));
+    CK(dev_axpby_f((float)(1.0 / sqrt(nn)), v1, 0.f, v1, nf, stream));
+    std::vector<double> al, be;
+    double prev_min = 0, prev_max = 0, tmin = 0, tmax = 0;
+    const int maxit = 600;
+    double beta_prev = 0.0;
+    for (int j = 0; j < maxit; j++) {
+        CK(wilson_f32(g, U32, (const float4 *)v1, (float4 *)tt, (float)m0_ker, 1, 1.f, nullptr, 0.f, stream));
+        CK(wilson_f32(g, U32, (const float4 *)tt, (float4 *)w, (float)m0_ker, 1, 1.f, nullptr, 0.f, stream));
+        if (j > 0) CK(dev_axpby_f((float)(-beta_prev), v0, 1.f, w, nf, stream));
+        double d2[2];
+        CK(dev_cdot_f(v1, w, nf, d_scal, rs, stream));
+        ST(fetch(d_scal, 2, d2));
+        const double alpha = d2[0];
+        CK(dev_axpby_f((float)(-alpha), v1, 1.f, w, nf, stream));
+        double bb;
+        ST(norm2_f(w, &bb));
+        const double beta = sqrt(bb);
+        al.push_back(alpha);
+        be.push_back(beta);
+        const int m = j + 1;
+        if (m % 10 == 0 || beta == 0.0) {
+            tmin = tridiag_eig(al, be, m, 0);
+            tmax = tridiag_eig(al, be, m, m - 1);
+            if (m >= 30 && fabs(tmin - prev_min) <= 1e-4 * tmin && fabs(tmax - prev_max) <= 1e-5 * tmax) break;
+            prev_min = tmin;
+            prev_max = tmax;
+        }
+        if (beta == 0.0) break;
+        // v0 <- v1, v1 <- w / beta
+        CK(cudaMemcpyAsync(v0, v1, nf * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+        CK(dev_axpby_f((float)(1.0 / beta), w, 0.f, v1, nf, stream));
+        beta_prev = beta;
+    }
+    if (!(tmin > 0) || !(tmax > tmin)) {
+        err = "Lanczos could not bound the spectrum of Q^2 (Q singular?)";
+        return OVL_EINVAL;
+    }
+    *lmin = sqrt(tmin);
+    *lmax = sqrt(tmax);
+    return OVL_OK;
+}
+
+// sigma~_max of D_W(0) by power iteration; sigma~_min = 8 - sigma~_max rounded up to
+// one decimal (Sec. 5.1).
+ovl_status Ctx::sigma_min_estimate(double *smin) {
+    Ctx *c = this;
+    const long nf = n64;
+    void *buf;
+    ST(alloc(&buf, (size_t)nf * sizeof(float) * 2));
+    float *v = (float *)buf, *w = v + nf;
+    std::vector<float> h(nf);
+    uint64_t st = 0xD1B54A32D192ED03ull;
+    for (long i = 0; i < nf; i++) {
+        st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+        h[i] = (float)((double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    }
+    CK(cudaMemcpyAsync(v, h.data(), nf * sizeof(float), cudaMemcpyHostToDevice, stream));
+    double nn;
+    ST(norm2_f(v, &nn));
+    CK(dev_axpby_f((float)(1.0 / sqrt(nn)), v, 0.f, v, nf, stream));
+    double ray = 0.0;
+    for (int it = 0; it < 50; it++) {
+        CK(wilson_f32(g, U32, (const float4 *)v, (float4 *)w, 0.f, 0, 1.f, nullptr, 0.f, stream));
+        double d2[2];
+        CK(dev_cdot_f(v, w, nf, d_scal, rs, stream));
+        ST(fetch(d_scal, 2, d2));
+        ray = d2[0];
+        ST(norm2_f(w, &nn));
+        CK(dev_axpby_f((float)(1.0 / sqrt(nn)), w, 0.f, v, nf, stream));
+    }
+    *smin = ceil(10.0 * (8.0 - ray)) / 10.0;
+    return OVL_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Threads per site of the stencils (1 or 4) for this lattice shape: both variants of
+// each precision are timed with CUDA events on the context's stream and the faster is
+// kept. Results are cached per process and shape.
+#include <map>
+#include <mutex>
+#include <tuple>
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+ovl_status Ctx::autotune() {
+    Ctx *c = this;
+    const auto key = std::make_tuple(g.L[0], g.L[1], g.L[2], g.L[3]);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            g.tps64 = it->second.first;
+            g.tps32 = it->second.second;
+            return OVL_OK;
+        }
+    }
+    void *buf;
+    ST(alloc(&buf, (size_t)n64 * sizeof(float) * 2));
+    float4 *fa = (float4 *)buf, *fb = fa + (size_t)g.V * 6;
+    CK(cudaMemsetAsync(buf, 0, (size_t)n64 * sizeof(float) * 2, stream));
+    CK(cudaMemsetAsync(io_a, 0, (size_t)n64 * sizeof(double), stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int reps = g.V >= (1 << 20) ? 5 : 20;
+    float best[2][2];
+    for (int prec = 0; prec < 2; prec++) {
+        for (int v = 0; v < 2; v++) {
+            const int tps = v == 0 ? 1 : 4;
+            Geom gg = g;
+            gg.tps64 = gg.tps32 = tps;
+            for (int k = 0; k < 3 + reps; k++) {
+                if (k == 3) CK(cudaEventRecord(e0, stream));
+                if (prec == 0) CK(wilson_f64(gg, U64, io_a, io_b, m0_ker, 0, 1.0, nullptr, 0.0, stream));
+                else CK(wilson_f32(gg, U32, fa, fb, (float)m0_ker, 0, 1.f, nullptr, 0.f, stream));
+            }
+            CK(cudaEventRecord(e1, stream));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&best[prec][v], e0, e1));
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g.tps64 = best[0][1] < best[0][0] ? 4 : 1;
+    g.tps32 = best[1][1] < best[1][0] ? 4 : 1;
+    tune_ms[0] = best[0][0] / reps;
+    tune_ms[1] = best[0][1] / reps;
+    tune_ms[2] = best[1][0] / reps;
+    tune_ms[3] = best[1][1] / reps;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = std::make_pair(g.tps64, g.tps32);
+    }
+    cudaFree(buf);
+    allocs.erase(std::find(allocs.begin(), allocs.end(), buf));
+    return OVL_OK;
+}
+
+// ------------------------------------------------------------------ ABI
+extern "C" ovl_status ovl_zolotarev(double k, int n, double *d0, double *a, double *c, double *delta) {
+    if (!d0 || !a || !c || !delta) return OVL_EINVAL;
+    return zolotarev_host(k, n, d0, a, c, delta) == 0 ? OVL_OK : OVL_EINVAL;
+}
+
+ovl_status Ctx::set_zolotarev() {
+    const double k = lam_min / lam_max;
+    za.assign(npole, 0.0);
+    zc.assign(npole, 0.0);
+    if (zolotarev_host(k, npole, &zd0, za.data(), zc.data(), &zdelta) != 0) {
+        err = "Zolotarev coefficients: bad interval";
+        return OVL_EINVAL;
+    }
+    return OVL_OK;
+}
+
+static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], double rho_in, double mu,
+                              const ovl_params *pp, void *stream) {
+    if (pp) c->p = *pp;
+    else ovl_params_default(&c->p);
+    for (int m = 0; m < 4; m++) {
+        if (dims[m] < 2 || (dims[m] & 1)) {
+            c->err = "lattice extents must be even and >= 2";
+            return OVL_EINVAL;
+        }
+    }
+    ST(validate_params(c->p, dims, c->err));
+    if (!(mu > 0) || !(rho_in > 0) || !(mu < 2 * rho_in)) {
+        c->err = "need rho > 0 and 0 < mu < 2 rho";
+        return OVL_EINVAL;
+    }
+    long V = (long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V > (1L << 26)) {
+        c->err = "lattice too large";
+        return OVL_EINVAL;
+    }
+    for (int m = 0; m < 4; m++) c->g.L[m] = dims[m];
+    c->g.V = (int)V;
+    c->g.Vh = (int)(V / 2);
+    c->g.Lh3 = dims[3] / 2;
+    c->g.antiperiodic = c->p.antiperiodic;
+    c->n64 = V * 24;
+    c->m0_ker = -rho_in;
+    c->rho_in = rho_in;
+    c->mu = mu;
+    c->rho = (-mu / 2.0 + c->m0_ker) / (mu / 2.0 + c->m0_ker);   // Sec. 5
+    c->npole = c->p.n_poles;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+        c->own_stream = false;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    // pinned host scratch
+    CK(cudaMallocHost(&c->h_pinned, 1 << 16));
+    c->h_scal = (double *)c->h_pinned;
+    c->h_flag = (int *)((char *)c->h_pinned + 4096);
+    c->h_ms_small = (int *)((char *)c->h_pinned + 8192);
+    c->h_ms = (MsState *)((char *)c->h_pinned + 16384);
+    c->h_hist = (int *)((char *)c->h_pinned + 32768);
+    c->launch_mark = launches_total();
+    // device scratch
+    void *buf;
+    ST(c->alloc(&buf, sizeof(double) * kMaxRedValues * kMaxRedBlocks + 4096));
+    c->rs.partials = (double *)buf;
+    c->rs.counter = (unsigned *)((char *)buf + sizeof(double) * kMaxRedValues * kMaxRedBlocks);
+    c->d_flag = (int *)((char *)buf + sizeof(double) * kMaxRedValues * kMaxRedBlocks + 256);
+    CK(cudaMemsetAsync(buf, 0, sizeof(double) * kMaxRedValues * kMaxRedBlocks + 4096, c->stream));
+    ST(c->alloc(&buf, 4096));
+    c->d_scal = (double *)buf;
+    ST(c->alloc(&buf, sizeof(MsState)));
+    c->ms64_state = (MsState *)buf;
+    ST(c->alloc(&buf, sizeof(MsState)));
+    c->ms32_state = (MsState *)buf;
+    ST(c->alloc(&buf, (size_t)128 * 256 * 2 * sizeof(double)));
+    c->d_md_part = (double *)buf;
+    ST(c->alloc(&buf, (size_t)2 * 128 * sizeof(double)));
+    c->d_coef = (double *)buf;
+    // gauge field
+    ST(c->alloc((void **)&c->U64, (size_t)V * 4 * 6 * sizeof(double2)));
+    ST(c->alloc((void **)&c->U32, (size_t)V * 4 * 3 * sizeof(float4)));
+    ST(c->alloc((void **)&c->io_lex, (size_t)c->n64 * sizeof(double)));
+    ST(c->alloc((void **)&c->io_a, (size_t)c->n64 * sizeof(double)));
+    ST(c->alloc((void **)&c->io_b, (size_t)c->n64 * sizeof(double)));
+    const double *glex = gauge;
+    void *gtmp = nullptr;
+    if (!is_device_ptr(gauge)) {
+        const size_t gb = (size_t)V * 4 * 9 * 2 * sizeof(double);
+        ST(c->alloc(&gtmp, gb));
+        CK(cudaMemcpyAsync(gtmp, gauge, gb, cudaMemcpyHostToDevice, c->stream));
+        glex = (const double *)gtmp;
+    }
+    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+    CK(pack_gauge(c->g, glex, c->U64, c->U32, c->d_flag, 1e-10, c->stream));
+    CK(cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ST(c->sync());
+    if (gtmp) {
+        cudaFree(gtmp);
+        c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), gtmp));
+    }
+    if (*c->h_flag) {
+        c->err = "gauge field: some link is not SU(3) to 1e-10 (or holds NaN)";
+        return OVL_EINVAL;
+    }
+    c->g.tps64 = c->g.tps32 = 1;
+    if (c->p.stencil_tps) c->g.tps64 = c->g.tps32 = c->p.stencil_tps;
+    else ST(c->autotune());
+    // spectral interval of |Q|
+    if (c->p.lambda_min > 0) {
+        c->lam_min = c->p.lambda_min;
+        c->lam_max = c->p.lambda_max;
+        c->lam_estimated = false;
+    } else {
+        double lmin, lmax;
+        ST(c->lanczos_bounds(&lmin, &lmax));
+        c->lam_min = 0.9 * lmin;    // margins: Ritz values bound the extreme eigenvalues from inside
+        c->lam_max = 1.05 * lmax;
+        c->lam_estimated = true;
+    }
+    ST(c->set_zolotarev());
+    // preconditioner mass m0^def (Eq. default_m) unless given
+    ST(c->sigma_min_estimate(&c->sigma_min));
+    if (isnan(c->p.m0_prec)) c->m0_prec = (-c->m0_ker - c->sigma_min) * c->rho + c->m0_ker;
+    else c->m0_prec = c->p.m0_prec;
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_create(ovl_ctx **ctx, const double *gauge, const int dims[4], double rho_in, double mu,
+                                 const ovl_params *p, void *cuda_stream) {
+    if (!ctx) return OVL_EINVAL;
+    *ctx = nullptr;
+    if (!gauge || !dims) {
+        g_create_error = "ovl_create: NULL gauge or dims";
+        return OVL_EINVAL;
+    }
+    Ctx *c = new Ctx();
+    ovl_status s = create_impl(c, gauge, dims, rho_in, mu, p, cuda_stream);
+    if (s != OVL_OK) {
+        g_create_error = c->err;
+        delete c;
+        return s;
+    }
+    *ctx = reinterpret_cast<ovl_ctx *>(c);
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_destroy(ovl_ctx *ctx) {
+    delete reinterpret_cast<Ctx *>(ctx);
+    return OVL_OK;
+}
+
+extern "C" const char *ovl_last_error(const ovl_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return reinterpret_cast<const Ctx *>(ctx)->err.c_str();
+}
+
+extern "C" ovl_status ovl_info(const ovl_ctx *ctx, double *lambda_min, double *lambda_max, double *delta, double *rho,
+                               double *m0_ker, double *m0_prec, double *sigma_min) {
+    if (!ctx) return OVL_EINVAL;
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (lambda_min) *lambda_min = c->lam_min;
+    if (lambda_max) *lambda_max = c->lam_max;
+    if (delta) *delta = c->zdelta;
+    if (rho) *rho = c->rho;
+    if (m0_ker) *m0_ker = c->m0_ker;
+    if (m0_prec) *m0_prec = c->m0_prec;
+    if (sigma_min) *sigma_min = c->sigma_min;
+    return OVL_OK;
+}
+
+static ovl_status check_ctx_ptrs(Ctx *c, const void *a, const void *b) {
+    if (!c) return OVL_EINVAL;
+    if (!a || !b) {
+        c->err = "NULL vector argument";
+        return OVL_EINVAL;
+    }
+    return OVL_OK;
+}
+
+extern "C" ovl_status wilson_apply(ovl_ctx *ctx, double *out, const double *in, double m0) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    if (!isfinite(m0)) {
+        c->err = "m0 must be finite";
+        return OVL_EINVAL;
+    }
+    ST(c->import_vec(in, c->io_a));
+    CK(wilson_f64(c->g, c->U64, c->io_a, c->io_b, m0, 0, 1.0, nullptr, 0.0, c->stream));
+    return c->export_vec(c->io_b, out);
+}
+
+static ovl_status check_tol(Ctx *c, double tol) {
+    if (!(tol >= 1e-14 && tol < 1.0)) {
+        c->err = "tol must be in [1e-14, 1)";
+        return OVL_EINVAL;
+    }
+    return OVL_OK;
+}
+
+extern "C" ovl_status sign_apply(ovl_ctx *ctx, double *out, const double *in, double tol) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    ST(check_tol(c, tol));
+    ST(c->import_vec(in, c->io_a));
+    ST(c->sign64(c->io_a, c->io_b, tol, 0));
+    return c->export_vec(c->io_b, out);
+}
+
+extern "C" ovl_status ovl_apply(ovl_ctx *ctx, double *out, const double *in, double tol) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    ST(check_tol(c, tol));
+    ST(c->import_vec(in, c->io_a));
+    ST(c->sign64(c->io_a, c->io_b, tol, 1));
+    return c->export_vec(c->io_b, out);
+}
+
+extern "C" ovl_status ovl_solve(ovl_ctx *ctx, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, x, b));
+    if (n_rhs < 1) {
+        c->err = "n_rhs must be >= 1";
+        return OVL_EINVAL;
+    }
+    if (tol == 0.0) tol = c->p.tol_outer;
+    ST(check_tol(c, tol));
+    return solve_all(c, x, b, n_rhs, tol, stats);
+}
+
+extern "C" ovl_status ovl_prof_enable(ovl_ctx *ctx, int on) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return OVL_EINVAL;
+    if (on && !c->d_hist) {
+        c->hist_cap = c->p.max_ms_iter + kMaxChunk;
+        ST(c->alloc((void **)&c->d_hist, (size_t)c->hist_cap * sizeof(int)));
+    }
+    c->prof = on != 0;
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !out) return OVL_EINVAL;
+    out->launches = launches_total() - c->launch_mark;
+    out->stencil_ms = c->pacc.q_ms + c->pacc.r_ms;
+    out->stencil_launches = c->pacc.q_n + c->pacc.r_n;
+    out->stencil_bytes = c->pacc.q_bytes + c->pacc.r_bytes;
+    out->shifts_ms = c->pacc.s_ms;
+    out->shifts_launches = c->pacc.s_n;
+    out->shifts_bytes = c->pacc.s_bytes;
+    out->valid = c->pacc.valid ? 1 : 0;
+    if (reset) {
+        c->pacc = ProfAcc();
+        c->launch_mark = launches_total();
+    }
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, float *ms) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c) return OVL_EINVAL;
+    if (tps64) *tps64 = c->g.tps64;
+    if (tps32) *tps32 = c->g.tps32;
+    if (ms)
+        for (int k = 0; k < 4; k++) ms[k] = c->tune_ms[k];
+    return OVL_OK;
+}
+
+extern "C" ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, double m0, double tol, int *iters) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, x, b));
+    if (!isfinite(m0)) {
+        c->err = "m0 must be finite";
+        return OVL_EINVAL;
+    }
+    if (!(tol > 0 && tol < 1)) {
+        c->err = "tol must be in (0, 1)";
+        return OVL_EINVAL;
+    }
+    for (int m = 0; m < 4; m++) {
+        if (c->p.sap_block[m] < 2 || (c->p.sap_block[m] & 1) || c->g.L[m] % c->p.sap_block[m] ||
+            c->p.sap_block[0] * c->p.sap_block[1] * c->p.sap_block[2] * c->p.sap_block[3] > 256) {
+            c->err = "sap_block must be even, divide the lattice extent and hold <= 256 sites";
+            return OVL_EINVAL;
+        }
+    }
+    ST(c->import_vec(b, c->io_a));
+    int it = 0;
+    ST(wilson_solve_eo(c, c->io_a, c->io_b, m0, tol, &it));
+    if (iters) *iters = it;
+    return c->export_vec(c->io_b, x);
+}

@@ -1,0 +1,211 @@
+// Device-side building blocks: complex arithmetic, even-odd lattice geometry,
+// field storage formats and their loads/stores.
+//
+// Internal layouts (all even-odd, site-major structure-of-arrays so that a warp's
+// 32 consecutive sites read 32 consecutive 16-byte words):
+//   parity p = (x0+x1+x2+x3) & 1, checkerboard index i = s >> 1 where
+//   s = ((x0*L1+x1)*L2+x2)*L3+x3 (needs L3 even); Vh = V/2 sites per parity.
+//   FP64 spinor: double2 [p][12 spin-colour][Vh]         (192 B per site)
+//   FP32 spinor: float4  [p][6 pairs of spin-colour][Vh] ( 96 B per site)
+//   FP16 spinor: uint4 (8 halves) [p][3][Vh] + float norm [p][Vh] (48+4 B per site)
+//   FP64 link:   double2 [p][mu][6][Vh]   rows 0 and 1 of U_mu(x) (12 reals)
+//   FP32 link:   float4  [p][mu][3][Vh]
+// Row 2 of an SU(3) link is rebuilt in registers as conj(row0 x row1).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace ovl {
+
+template <typename R>
+struct cpx {
+    R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mk(R a, R b) { return cpx<R>{a, b}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator-(cpx<R> a) { return {-a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> conj(cpx<R> a) { return {a.re, -a.im}; }
+// i*a and -i*a
+template <typename R>
+__device__ __forceinline__ cpx<R> mul_i(cpx<R> a) { return {-a.im, a.re}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> mul_mi(cpx<R> a) { return {a.im, -a.re}; }
+// conj(a)*b
+template <typename R>
+__device__ __forceinline__ cpx<R> cmul_conj(cpx<R> a, cpx<R> b) {
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ R norm2(cpx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// Lattice geometry shared by all kernels.
+struct Geom {
+    int L[4];
+    int Lh3;    // L3 / 2
+    int Vh;     // V / 2
+    int V;
+    int antiperiodic;
+    int tps64, tps32;   // threads per site of the FP64 / FP32 stencils (1 or 4), chosen by the autotuner
+};
+
+// Coordinates of checkerboard site (p, i).
+__device__ __forceinline__ void eo_coords(const Geom &g, int p, int i, int x[4]) {
+    int x3h = i % g.Lh3;
+    int r = i / g.Lh3;
+    x[2] = r % g.L[2];
+    r /= g.L[2];
+    x[1] = r % g.L[1];
+    x[0] = r / g.L[1];
+    int b = (p + x[0] + x[1] + x[2]) & 1;
+    x[3] = 2 * x3h + b;
+}
+
+__device__ __forceinline__ int eo_index(const Geom &g, const int x[4]) {
+    return (((x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3]) >> 1;
+}
+
+// ---------------------------------------------------------------------------
+// Field storage formats. Each provides load/store of one site's 12 spin-colour
+// components as cpx<R>, R the arithmetic type.
+// ---------------------------------------------------------------------------
+struct SpinorF64 {
+    using store_t = double2;
+    static constexpr int chunks = 12;
+};
+struct SpinorF32 {
+    using store_t = float4;
+    static constexpr int chunks = 6;
+};
+
+template <typename R>
+__device__ __forceinline__ void load_spinor(const double2 *__restrict__ f, int Vh, int p, int i, cpx<R> s[12]) {
+    const double2 *b = f + (size_t)p * 12 * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+        double2 v = __ldg(b + (size_t)c * Vh);
+        s[c] = cpx<R>{(R)v.x, (R)v.y};
+    }
+}
+template <typename R>
+__device__ __forceinline__ void load_spinor(const float4 *__restrict__ f, int Vh, int p, int i, cpx<R> s[12]) {
+    const float4 *b = f + (size_t)p * 6 * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+        float4 v = __ldg(b + (size_t)c * Vh);
+        s[2 * c] = cpx<R>{(R)v.x, (R)v.y};
+        s[2 * c + 1] = cpx<R>{(R)v.z, (R)v.w};
+    }
+}
+template <typename R>
+__device__ __forceinline__ void store_spinor(double2 *__restrict__ f, int Vh, int p, int i, const cpx<R> s[12]) {
+    double2 *b = f + (size_t)p * 12 * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 12; c++) b[(size_t)c * Vh] = make_double2((double)s[c].re, (double)s[c].im);
+}
+template <typename R>
+__device__ __forceinline__ void store_spinor(float4 *__restrict__ f, int Vh, int p, int i, const cpx<R> s[12]) {
+    float4 *b = f + (size_t)p * 6 * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 6; c++)
+        b[(size_t)c * Vh] = make_float4((float)s[2 * c].re, (float)s[2 * c].im, (float)s[2 * c + 1].re,
+                                        (float)s[2 * c + 1].im);
+}
+
+// Half-precision spinor: 24 halves per site in 3 uint4 words, scaled by a per-site
+// FP32 norm (the largest |component| of the site).
+struct HalfSpinor {
+    uint4 *v;
+    float *norm;
+};
+struct HalfSpinorC {
+    const uint4 *v;
+    const float *norm;
+};
+
+template <typename R>
+__device__ __forceinline__ void load_spinor(HalfSpinorC f, int Vh, int p, int i, cpx<R> s[12]) {
+    const uint4 *b = f.v + (size_t)p * 3 * Vh + i;
+    const float nrm = __ldg(f.norm + (size_t)p * Vh + i);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        uint4 w = __ldg(b + (size_t)c * Vh);
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            __half2 h = *reinterpret_cast<const __half2 *>(&u[q]);
+            float2 fl = __half22float2(h);
+            s[4 * c + q] = cpx<R>{(R)(fl.x * nrm), (R)(fl.y * nrm)};
+        }
+    }
+}
+template <typename R>
+__device__ __forceinline__ void store_spinor(HalfSpinor f, int Vh, int p, int i, const cpx<R> s[12]) {
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < 12; c++) m = fmaxf(m, fmaxf(fabsf((float)s[c].re), fabsf((float)s[c].im)));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+    uint4 *b = f.v + (size_t)p * 3 * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        uint32_t u[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            __half2 h = __floats2half2_rn((float)s[4 * c + q].re * inv, (float)s[4 * c + q].im * inv);
+            u[q] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        b[(size_t)c * Vh] = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+    f.norm[(size_t)p * Vh + i] = m;
+}
+
+// Links: rows 0 and 1 stored, row 2 = conj(row0 x row1).
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(cpx<R> u[3][3]) {
+    u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+    u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+    u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+}
+template <typename R>
+__device__ __forceinline__ void load_link(const double2 *__restrict__ g, int Vh, int p, int mu, int i, cpx<R> u[3][3]) {
+    const double2 *b = g + ((size_t)(p * 4 + mu) * 6) * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+        double2 v = __ldg(b + (size_t)c * Vh);
+        u[c / 3][c % 3] = cpx<R>{(R)v.x, (R)v.y};
+    }
+    reconstruct_row2(u);
+}
+template <typename R>
+__device__ __forceinline__ void load_link(const float4 *__restrict__ g, int Vh, int p, int mu, int i, cpx<R> u[3][3]) {
+    const float4 *b = g + ((size_t)(p * 4 + mu) * 3) * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float4 v = __ldg(b + (size_t)c * Vh);
+        u[(2 * c) / 3][(2 * c) % 3] = cpx<R>{(R)v.x, (R)v.y};
+        u[(2 * c + 1) / 3][(2 * c + 1) % 3] = cpx<R>{(R)v.z, (R)v.w};
+    }
+    reconstruct_row2(u);
+}
+
+// gamma_5 = diag(-1,-1,+1,+1) in the chiral basis: flips spins 0 and 1.
+template <typename R>
+__device__ __forceinline__ void apply_g5(cpx<R> s[12]) {
+#pragma unroll
+    for (int c = 0; c < 6; c++) s[c] = -s[c];
+}
+
+}  // namespace ovl

@@ -1,0 +1,233 @@
+// Layout conversion and the Wilson-Dirac stencil kernels (Eq. Wilson-Dirac).
+#include "internal.h"
+#include "reduce.cuh"
+#include "wilson_quad.cuh"
+#include "wilson_site.cuh"
+
+#include <atomic>
+
+namespace ovl {
+
+static std::atomic<long> g_launches{0};
+static thread_local bool g_counting = true;
+void count_launches(long n) {
+    if (g_counting) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+void set_launch_counting(bool on) { g_counting = on; }
+
+// ------------------------------------------------------------------ gauge upload
+// One thread per (site, mu): SU(3) check, then rows 0 and 1 into both precisions.
+__global__ void k_pack_gauge(Geom g, const double2 *__restrict__ lex, double2 *u64, float4 *u32, int *bad,
+                             double tol) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)g.V * 4) return;
+    const int s = (int)(t >> 2), mu = (int)(t & 3);
+    cpx<double> u[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            double2 v = lex[(size_t)t * 9 + a * 3 + b];
+            u[a][b] = cpx<double>{v.x, v.y};
+        }
+    // unitarity: max |(U U^H - I)_ab|; det U = 1
+    double err = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            cpx<double> d = cmul_conj(u[b][0], u[a][0]) + cmul_conj(u[b][1], u[a][1]) + cmul_conj(u[b][2], u[a][2]);
+            if (a == b) d.re -= 1.0;
+            err = fmax(err, sqrt(norm2(d)));
+        }
+    cpx<double> det = u[0][0] * (u[1][1] * u[2][2] - u[1][2] * u[2][1]) -
+                      u[0][1] * (u[1][0] * u[2][2] - u[1][2] * u[2][0]) +
+                      u[0][2] * (u[1][0] * u[2][1] - u[1][1] * u[2][0]);
+    det.re -= 1.0;
+    err = fmax(err, sqrt(norm2(det)));
+    if (!(err <= tol)) atomicExch(bad, 1);   // also catches NaN
+    int x[4];
+    int r = s;
+    x[3] = r % g.L[3]; r /= g.L[3];
+    x[2] = r % g.L[2]; r /= g.L[2];
+    x[1] = r % g.L[1]; x[0] = r / g.L[1];
+    const int p = (x[0] + x[1] + x[2] + x[3]) & 1, i = s >> 1;
+    double2 *d64 = u64 + ((size_t)(p * 4 + mu) * 6) * g.Vh + i;
+#pragma unroll
+    for (int c = 0; c < 6; c++) d64[(size_t)c * g.Vh] = make_double2(u[c / 3][c % 3].re, u[c / 3][c % 3].im);
+    float4 *d32 = u32 + ((size_t)(p * 4 + mu) * 3) * g.Vh + i;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const cpx<double> e0 = u[(2 * c) / 3][(2 * c) % 3], e1 = u[(2 * c + 1) / 3][(2 * c + 1) % 3];
+        d32[(size_t)c * g.Vh] = make_float4((float)e0.re, (float)e0.im, (float)e1.re, (float)e1.im);
+    }
+}
+
+cudaError_t pack_gauge(const Geom &g, const double *lex, double2 *u64, float4 *u32, int *bad, double tol,
+                       cudaStream_t st) {
+    k_pack_gauge<<<plain_grid((long)g.V * 4), kBlock, 0, st>>>(g, (const double2 *)lex, u64, u32, bad, tol);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ spinor layout
+__device__ __forceinline__ void lex_to_eo(const Geom &g, int s, int &p, int &i) {
+    int r = s;
+    int x3 = r % g.L[3]; r /= g.L[3];
+    int x2 = r % g.L[2]; r /= g.L[2];
+    int x1 = r % g.L[1];
+    int x0 = r / g.L[1];
+    p = (x0 + x1 + x2 + x3) & 1;
+    i = s >> 1;
+}
+
+__global__ void k_pack_spinor_f64(Geom g, double2 *dst, const double2 *__restrict__ lex) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    int p, i;
+    lex_to_eo(g, s, p, i);
+    cpx<double> v[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+        double2 e = lex[(size_t)s * 12 + c];
+        v[c] = cpx<double>{e.x, e.y};
+    }
+    store_spinor<double>(dst, g.Vh, p, i, v);
+}
+
+__global__ void k_unpack_spinor_f64(Geom g, double2 *lex, const double2 *__restrict__ src) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    int p, i;
+    lex_to_eo(g, s, p, i);
+    cpx<double> v[12];
+    load_spinor<double>(src, g.Vh, p, i, v);
+#pragma unroll
+    for (int c = 0; c < 12; c++) lex[(size_t)s * 12 + c] = make_double2(v[c].re, v[c].im);
+}
+
+cudaError_t pack_spinor_f64(const Geom &g, double2 *dst, const double *lex, cudaStream_t st) {
+    k_pack_spinor_f64<<<plain_grid(g.V), kBlock, 0, st>>>(g, dst, (const double2 *)lex);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t unpack_spinor_f64(const Geom &g, double *lex, const double2 *src, cudaStream_t st) {
+    k_unpack_spinor_f64<<<plain_grid(g.V), kBlock, 0, st>>>(g, (double2 *)lex, src);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// FP64 <-> FP32 even-odd spinors (double2 [p][12][Vh] <-> float4 [p][6][Vh])
+__global__ void k_spinor_d2f(Geom g, const double2 *__restrict__ a, float4 *__restrict__ b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.V) return;
+    const int p = t >= g.Vh, i = t - p * g.Vh;
+    cpx<float> v[12];
+    load_spinor<float>(a, g.Vh, p, i, v);
+    store_spinor<float>(b, g.Vh, p, i, v);
+}
+__global__ void k_spinor_f2d(Geom g, const float4 *__restrict__ a, double2 *__restrict__ b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.V) return;
+    const int p = t >= g.Vh, i = t - p * g.Vh;
+    cpx<double> v[12];
+    load_spinor<double>(a, g.Vh, p, i, v);
+    store_spinor<double>(b, g.Vh, p, i, v);
+}
+cudaError_t spinor_d2f(const Geom &g, const double2 *a, float4 *b, cudaStream_t st) {
+    k_spinor_d2f<<<plain_grid(g.V), kBlock, 0, st>>>(g, a, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t spinor_f2d(const Geom &g, const float4 *a, double2 *b, cudaStream_t st) {
+    k_spinor_f2d<<<plain_grid(g.V), kBlock, 0, st>>>(g, a, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ stencil
+// out = a [g5] D_W(m0) in + b z, one thread per site of the full lattice
+// (threads [0, Vh) even sites, [Vh, V) odd sites).
+template <typename R, typename LT, typename ST>
+__global__ void __launch_bounds__(kBlock) k_wilson(Geom g, const LT *__restrict__ U, const ST *__restrict__ in,
+                                                   ST *__restrict__ out, R m4, int g5, R a,
+                                                   const ST *z, R b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.V) return;
+    const int p = t >= g.Vh, i = t - p * g.Vh;
+    cpx<R> hop[12], own[12], res[12];
+    wilson_hop<R>(g, U, in, p, i, hop);
+    load_spinor<R>(in, g.Vh, p, i, own);
+    wilson_combine<R>(m4, own, hop, res);
+    if (g5) apply_g5(res);
+    if (z) {
+        cpx<R> zz[12];
+        load_spinor<R>(z, g.Vh, p, i, zz);
+#pragma unroll
+        for (int c = 0; c < 12; c++) res[c] = a * res[c] + b * zz[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; c++) res[c] = a * res[c];
+    }
+    store_spinor<R>(out, g.Vh, p, i, res);
+}
+
+// Same with four threads per site (thread q of a quad owns direction mu = q and the
+// storage words j with j % 4 == q of the output).
+template <typename R, typename LT, typename ST>
+__global__ void __launch_bounds__(kBlock) k_wilson4(Geom g, const LT *__restrict__ U, const ST *__restrict__ in,
+                                                    ST *__restrict__ out, R m4, int g5, R a, const ST *z, R b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s0 = t >> 2, q = t & 3;
+    const int s = s0 < g.V ? s0 : g.V - 1;   // quads past the end compute a copy, store nothing
+    const int p = s >= g.Vh, i = s - p * g.Vh;
+    cpx<R> acc[12];
+    wilson_hop_dir<R>(g, U, in, p, i, q, acc);
+    quad_allreduce(acc);
+    if (s0 >= g.V) return;
+    using C = Chunk<ST>;
+#pragma unroll
+    for (int j = 0; j < C::NC; j++) {
+        if ((j & 3) != q) continue;
+        cpx<R> own[C::CPC], res[C::CPC];
+        C::template load<R>(in, g.Vh, p, i, j, own);
+#pragma unroll
+        for (int e = 0; e < C::CPC; e++) {
+            const int cix = j * C::CPC + e;
+            res[e] = m4 * own[e] - (R)0.5 * acc[cix];
+            if (g5 && cix < 6) res[e] = -res[e];
+            res[e] = a * res[e];
+        }
+        if (z) {
+            cpx<R> zz[C::CPC];
+            C::template load<R>(z, g.Vh, p, i, j, zz);
+#pragma unroll
+            for (int e = 0; e < C::CPC; e++) res[e] = res[e] + b * zz[e];
+        }
+        C::template store<R>(out, g.Vh, p, i, j, res);
+    }
+}
+
+cudaError_t wilson_f64(const Geom &g, const double2 *U, const double2 *in, double2 *out, double m0, int g5,
+                       double a, const double2 *z, double b, cudaStream_t st) {
+    if (g.tps64 == 4)
+        k_wilson4<double, double2, double2><<<plain_grid(4L * g.V), kBlock, 0, st>>>(g, U, in, out, m0 + 4.0, g5,
+                                                                                     a, z, b);
+    else
+        k_wilson<double, double2, double2><<<plain_grid(g.V), kBlock, 0, st>>>(g, U, in, out, m0 + 4.0, g5, a, z, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t wilson_f32(const Geom &g, const float4 *U, const float4 *in, float4 *out, float m0, int g5,
+                       float a, const float4 *z, float b, cudaStream_t st) {
+    if (g.tps32 == 4)
+        k_wilson4<float, float4, float4><<<plain_grid(4L * g.V), kBlock, 0, st>>>(g, U, in, out, m0 + 4.0f, g5, a,
+                                                                                  z, b);
+    else
+        k_wilson<float, float4, float4><<<plain_grid(g.V), kBlock, 0, st>>>(g, U, in, out, m0 + 4.0f, g5, a, z, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace ovl

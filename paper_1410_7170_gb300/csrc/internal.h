@@ -1,0 +1,135 @@
+// Internal interfaces between the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace ovl {
+
+constexpr int kMaxPoles = 64;
+constexpr int kBlock = 256;             // threads per block of site-parallel kernels
+constexpr int kMaxRedBlocks = 4096;     // cap on blocks of a reducing kernel (grid-stride beyond)
+constexpr int kMaxRedValues = 4;        // doubles reduced by one kernel
+
+// Scratch of the deterministic two-level reductions: per-block partial sums, and
+// a counter the last finishing block uses to find that it is last.
+struct RedScratch {
+    double *partials;      // [kMaxRedValues][kMaxRedBlocks]
+    unsigned *counter;     // one word, zero between launches
+};
+
+inline int red_grid(long n_threads) {
+    long b = (n_threads + kBlock - 1) / kBlock;
+    if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+inline int plain_grid(long n_threads) {
+    long b = (n_threads + kBlock - 1) / kBlock;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------- layouts / gauge
+// lex: V*4*9 complex doubles [s][mu][a][b]. Writes the FP64 and FP32 12-real copies;
+// sets *bad to 1 if some link misses unitarity or det = 1 by more than tol.
+cudaError_t pack_gauge(const Geom &g, const double *lex, double2 *u64, float4 *u32, int *bad, double tol,
+                       cudaStream_t st);
+// lex spinor [s][12] complex doubles <-> internal even-odd layouts
+cudaError_t pack_spinor_f64(const Geom &g, double2 *dst, const double *lex, cudaStream_t st);
+cudaError_t unpack_spinor_f64(const Geom &g, double *lex, const double2 *src, cudaStream_t st);
+
+// even-odd FP64 <-> FP32 spinor conversion
+cudaError_t spinor_d2f(const Geom &g, const double2 *a, float4 *b, cudaStream_t st);
+cudaError_t spinor_f2d(const Geom &g, const float4 *a, double2 *b, cudaStream_t st);
+
+// ---------------------------------------------------------------- stencils
+// out = a * [gamma5] D_W(m0) in + b * z   (z may be NULL; then b is ignored)
+cudaError_t wilson_f64(const Geom &g, const double2 *U, const double2 *in, double2 *out, double m0, int g5,
+                       double a, const double2 *z, double b, cudaStream_t st);
+cudaError_t wilson_f32(const Geom &g, const float4 *U, const float4 *in, float4 *out, float m0, int g5,
+                       float a, const float4 *z, float b, cudaStream_t st);
+
+// ---------------------------------------------------------------- BLAS-1 (flat arrays of n doubles)
+// Reductions return through device memory `res` (written by the last block).
+cudaError_t dev_norm2(const double *x, long n, double *res, RedScratch rs, cudaStream_t st);
+// res[0] = Re <x,y>, res[1] = Im <x,y> (complex interleaved, n doubles = n/2 complex)
+cudaError_t dev_cdot(const double *x, const double *y, long n, double *res, RedScratch rs, cudaStream_t st);
+// y = a x + b y (real a, b)
+cudaError_t dev_axpby(double a, const double *x, double b, double *y, long n, cudaStream_t st);
+// y += (ar + i ai) x  (complex, interleaved)
+cudaError_t dev_caxpy(double ar, double ai, const double *x, double *y, long n, cudaStream_t st);
+// Arnoldi helpers: out[2k..2k+1] = <v_k, w> for k < m (v_k = base + k*stride), deterministic
+cudaError_t dev_multidot(const double *base, long stride, int m, const double *w, long n, double *out,
+                         double *partials, cudaStream_t st);
+// w += sum_k c_k v_k, c complex interleaved in device memory (m <= 128)
+cudaError_t dev_multiaxpy(const double *base, long stride, int m, const double *c, double *w, long n,
+                          cudaStream_t st);
+// float <-> double conversion of flat arrays (same element order)
+cudaError_t dev_d2f(const double *x, float *y, long n, cudaStream_t st);
+cudaError_t dev_f2d(const float *x, double *y, long n, cudaStream_t st);
+// y = a*x + b*y on floats
+cudaError_t dev_axpby_f(float a, const float *x, float b, float *y, long n, cudaStream_t st);
+cudaError_t dev_norm2_f(const float *x, long n, double *res, RedScratch rs, cudaStream_t st);
+cudaError_t dev_cdot_f(const float *x, const float *y, long n, double *res, RedScratch rs, cudaStream_t st);
+// multi-dot / multi-axpy with float vectors (accumulation in double)
+cudaError_t dev_multidot_f(const float *base, long stride, int m, const float *w, long n, double *out,
+                           double *partials, cudaStream_t st);
+cudaError_t dev_multiaxpy_f(const float *base, long stride, int m, const double *c, float *w, long n,
+                            cudaStream_t st);
+// Finite check of a flat array: *flag = 1 if some entry is NaN/Inf.
+cudaError_t dev_nonfinite(const double *x, long n, int *flag, cudaStream_t st);
+
+// ---------------------------------------------------------------- multishift CG
+// Device-side state of one multishift solve (Q^2 + sigma_l) x_l = b, l < n, with the
+// Zolotarev accumulation y = b + sum_l w_l x_l. sigma[0] is the base (smallest) shift.
+struct MsState {
+    int n;                     // shifts
+    int iter;                  // iterations done
+    int done;                  // 1: all shifts converged (kernels then do nothing)
+    int status;                // 0 ok, 1 breakdown / non-finite scalar
+    double bb;                 // ||b||^2
+    double rr;                 // ||r_k||^2 (base residual)
+    double alpha, alpha_prev, beta_prev;
+    double tol;                // target relative accuracy of the rational function
+    double sigma[kMaxPoles];   // shifts
+    double w[kMaxPoles];       // weights of x_l in y
+    double crit[kMaxPoles];    // drop shift l when crit_l * |zeta_l| * ||r|| <= tol * ||b||
+    double zeta[kMaxPoles], zeta_prev[kMaxPoles];
+    double alpha_l[kMaxPoles], beta_l[kMaxPoles];   // per-shift step sizes for this iteration
+    int active[kMaxPoles];
+    int *hist;                 // optional: hist[k] = shifts updated in iteration k (instrumentation)
+    int hist_cap;
+};
+
+// Workspace vectors of a multishift solve, in storage type ST.
+template <typename ST>
+struct MsVectors {
+    ST *r;       // base residual
+    ST *t;       // Q p_0
+    ST *y;       // accumulated rational function argument
+    ST *p;       // n search directions, p[l] at p + l * stride
+    long stride; // elements of ST per vector
+};
+
+// One multishift iteration = four launches (Q p, residual update, shift updates, retire).
+// ev (optional, 4 events): recorded before/between/after the first three launches;
+// ev_flags is passed to cudaEventRecordWithFlags (cudaEventRecordExternal inside graphs).
+cudaError_t ms_init_f64(const Geom &g, int n, MsState *s, MsVectors<double2> v, const double2 *b, RedScratch rs,
+                        cudaStream_t st);
+cudaError_t ms_iter_f64(const Geom &g, const double2 *U, double m0, MsState *s, MsVectors<double2> v,
+                        RedScratch rs, cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
+cudaError_t ms_init_f32(const Geom &g, int n, MsState *s, MsVectors<float4> v, const float4 *b, RedScratch rs,
+                        cudaStream_t st);
+cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, MsVectors<float4> v,
+                        RedScratch rs, cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
+
+// Process-wide count of kernel launches issued by the library (instrumentation).
+void count_launches(long n);
+long launches_total();
+void set_launch_counting(bool on);
+
+// ---------------------------------------------------------------- host Zolotarev
+int zolotarev_host(double k, int n, double *d0, double *a, double *c, double *delta);
+
+}  // namespace ovl

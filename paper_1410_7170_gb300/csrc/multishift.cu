@@ -1,0 +1,385 @@
+// Multishift conjugate gradients for the Zolotarev partial fractions of sign(Q).
+//
+// The n shifted systems (Q^2 + sigma_l) x_l = b share one Krylov space. The base
+// system (smallest shift sigma_0) runs plain CG; shift l keeps its own direction
+// p_l and scalars from the shifted-CG recurrences (Jegerlehner, hep-lat/9612014;
+// Frommer, "BiCGStab(l) for families of shifted linear systems", 2003):
+//
+//   zeta_{k+1} = zeta_k zeta_{k-1} a_{k-1} /
+//                ( a_k b_{k-1} (zeta_{k-1} - zeta_k) + zeta_{k-1} a_{k-1} (1 + (sigma_l - sigma_0) a_k) )
+//   a^l_k = a_k zeta_{k+1}/zeta_k,   b^l_k = b_k (zeta_{k+1}/zeta_k)^2
+//   x_l += a^l_k p_l,   p_l = zeta_{k+1} r_{k+1} + b^l_k p_l,   r^l = zeta r.
+//
+// x_l is never stored: the rational function needs only y = b + sum_l w_l x_l, so
+// each iteration adds w_l a^l_k p_l to y. Shift l is dropped once its residual
+// bound crit_l |zeta_l| ||r|| falls below tol ||b||.
+//
+// One iteration = three kernels, all scalars stay on the device:
+//   ms_q:      t = Q p_0 (stencil with gamma5),       reduce ||t||^2, ||p_0||^2 -> alpha
+//   ms_r:      r -= alpha (gamma5 D_W t + sigma_0 p_0), reduce ||r||^2 -> beta, shift scalars
+//   ms_shifts: y += sum_l w_l a^l p_l ; p_l = zeta_l r + b^l p_l   (pure streaming)
+// (p_0, Q^2 p_0) = ||Q p_0||^2 because Q is Hermitian (Eq. gamma_5_symmetry).
+// After convergence (state->done) every kernel returns at once, so a fixed number
+// of iterations can be queued or captured in a CUDA graph without host round trips.
+#include <math.h>
+
+#include "internal.h"
+#include "reduce.cuh"
+#include "wilson_quad.cuh"
+#include "wilson_site.cuh"
+
+namespace ovl {
+
+namespace {
+
+struct AlphaFin {
+    MsState *s;
+    __device__ void operator()(const double *v) const {
+        const double pAp = v[0] + s->sigma[0] * v[1];
+        const double a = s->rr / pAp;
+        if (!(pAp > 0.0) || !isfinite(a)) {
+            s->status = 1;
+            s->done = 1;
+            return;
+        }
+        s->alpha = a;
+    }
+};
+
+struct ShiftFin {
+    MsState *s;
+    __device__ void operator()(const double *v) const {
+        const double rr_new = v[0];
+        const double a = s->alpha, ap = s->alpha_prev, bp = s->beta_prev;
+        const double beta = rr_new / s->rr;
+        if (!isfinite(beta)) {
+            s->status = 1;
+            s->done = 1;
+            return;
+        }
+        const double rnorm = sqrt(rr_new), bnorm = sqrt(s->bb);
+        int any = 0;
+        for (int l = 0; l < s->n; l++) {
+            if (!s->active[l]) {
+                s->alpha_l[l] = 0.0;
+                continue;
+            }
+            double zn;
+            if (l == 0) {
+                zn = 1.0;
+            } else {
+                const double z = s->zeta[l], zp = s->zeta_prev[l];
+                const double den = a * bp * (zp - z) + zp * ap * (1.0 + (s->sigma[l] - s->sigma[0]) * a);
+                zn = (den != 0.0) ? z * zp * ap / den : 0.0;
+            }
+            const double ratio = (s->zeta[l] != 0.0) ? zn / s->zeta[l] : 0.0;
+            s->alpha_l[l] = a * ratio;
+            s->beta_l[l] = beta * ratio * ratio;
+            s->zeta_prev[l] = s->zeta[l];
+            s->zeta[l] = zn;
+            // residual bound after this iteration's update: drop the shift next time
+            if (s->crit[l] * fabs(zn) * rnorm <= s->tol * bnorm) s->active[l] = 2;   // last update
+            else any = 1;
+        }
+        // the base direction p_0 drives the Krylov space: keep it while any shift is live
+        if (any && s->active[0] == 2) s->active[0] = 1;
+        if (s->hist && s->iter < s->hist_cap) {
+            int nu = 0;
+            for (int l = 0; l < s->n; l++) nu += s->active[l] != 0;
+            s->hist[s->iter] = nu;
+        }
+        s->alpha_prev = a;
+        s->beta_prev = beta;
+        s->rr = rr_new;
+        s->iter += 1;
+        if (!any) s->done = 2;   // finish this iteration's shift updates, then stop
+    }
+};
+
+// t = gamma5 D_W(m) p0 ; reduce ||t||^2, ||p0||^2
+template <typename R, typename LT, typename ST>
+__global__ void __launch_bounds__(kBlock) k_ms_q(Geom g, const LT *__restrict__ U, R m4, MsState *s,
+                                                 const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs) {
+    if (s->done) return;
+    double v[2] = {0.0, 0.0};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
+        const int p = k >= g.Vh, i = k - p * g.Vh;
+        cpx<R> hop[12], own[12], res[12];
+        wilson_hop<R>(g, U, p0, p, i, hop);
+        load_spinor<R>(p0, g.Vh, p, i, own);
+        wilson_combine<R>(m4, own, hop, res);
+        apply_g5(res);
+        store_spinor<R>(t, g.Vh, p, i, res);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            v[0] += (double)norm2(res[c]);
+            v[1] += (double)norm2(own[c]);
+        }
+    }
+    grid_reduce<2>(v, rs, AlphaFin{s});
+}
+
+// r -= alpha (gamma5 D_W(m) t + sigma0 p0) ; reduce ||r||^2 ; shift scalars
+template <typename R, typename LT, typename ST>
+__global__ void __launch_bounds__(kBlock) k_ms_r(Geom g, const LT *__restrict__ U, R m4, MsState *s,
+                                                 const ST *__restrict__ t, const ST *__restrict__ p0,
+                                                 ST *__restrict__ r, RedScratch rs) {
+    if (s->done) return;
+    const R alpha = (R)s->alpha, sig0 = (R)s->sigma[0];
+    double v[1] = {0.0};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
+        const int p = k >= g.Vh, i = k - p * g.Vh;
+        cpx<R> hop[12], own[12], res[12], pp[12], rv[12];
+        wilson_hop<R>(g, U, t, p, i, hop);
+        load_spinor<R>(t, g.Vh, p, i, own);
+        wilson_combine<R>(m4, own, hop, res);
+        apply_g5(res);
+        load_spinor<R>(p0, g.Vh, p, i, pp);
+        load_spinor<R>(r, g.Vh, p, i, rv);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            rv[c] = rv[c] - alpha * (res[c] + sig0 * pp[c]);
+            v[0] += (double)norm2(rv[c]);
+        }
+        store_spinor<R>(r, g.Vh, p, i, rv);
+    }
+    grid_reduce<1>(v, rs, ShiftFin{s});
+}
+
+// Four-threads-per-site versions (see wilson_quad.cuh). The loops stride by whole
+// blocks so every lane of a warp runs the same trip count (the shuffles need all lanes).
+template <typename R, typename LT, typename ST>
+__global__ void __launch_bounds__(kBlock) k_ms_q4(Geom g, const LT *__restrict__ U, R m4, MsState *s,
+                                                  const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs) {
+    if (s->done) return;
+    using C = Chunk<ST>;
+    double v[2] = {0.0, 0.0};
+    const long nthr = 4L * g.V;
+    for (long base = (long)blockIdx.x * blockDim.x; base < nthr; base += (long)gridDim.x * blockDim.x) {
+        const long tt = base + threadIdx.x;
+        const int s0 = (int)(tt >> 2), q = (int)(tt & 3);
+        const int site = s0 < g.V ? s0 : g.V - 1;
+        const int p = site >= g.Vh, i = site - p * g.Vh;
+        cpx<R> acc[12];
+        wilson_hop_dir<R>(g, U, p0, p, i, q, acc);
+        quad_allreduce(acc);
+        if (s0 >= g.V) continue;
+#pragma unroll
+        for (int j = 0; j < C::NC; j++) {
+            if ((j & 3) != q) continue;
+            cpx<R> own[C::CPC], res[C::CPC];
+            C::template load<R>(p0, g.Vh, p, i, j, own);
+#pragma unroll
+            for (int e = 0; e < C::CPC; e++) {
+                const int cix = j * C::CPC + e;
+                res[e] = m4 * own[e] - (R)0.5 * acc[cix];
+                if (cix < 6) res[e] = -res[e];
+                v[0] += (double)norm2(res[e]);
+                v[1] += (double)norm2(own[e]);
+            }
+            C::template store<R>(t, g.Vh, p, i, j, res);
+        }
+    }
+    grid_reduce<2>(v, rs, AlphaFin{s});
+}
+
+template <typename R, typename LT, typename ST>
+__global__ void __launch_bounds__(kBlock) k_ms_r4(Geom g, const LT *__restrict__ U, R m4, MsState *s,
+                                                  const ST *__restrict__ t, const ST *__restrict__ p0,
+                                                  ST *__restrict__ r, RedScratch rs) {
+    if (s->done) return;
+    using C = Chunk<ST>;
+    const R alpha = (R)s->alpha, sig0 = (R)s->sigma[0];
+    double v[1] = {0.0};
+    const long nthr = 4L * g.V;
+    for (long base = (long)blockIdx.x * blockDim.x; base < nthr; base += (long)gridDim.x * blockDim.x) {
+        const long tt = base + threadIdx.x;
+        const int s0 = (int)(tt >> 2), q = (int)(tt & 3);
+        const int site = s0 < g.V ? s0 : g.V - 1;
+        const int p = site >= g.Vh, i = site - p * g.Vh;
+        cpx<R> acc[12];
+        wilson_hop_dir<R>(g, U, t, p, i, q, acc);
+        quad_allreduce(acc);
+        if (s0 >= g.V) continue;
+#pragma unroll
+        for (int j = 0; j < C::NC; j++) {
+            if ((j & 3) != q) continue;
+            cpx<R> own[C::CPC], pp[C::CPC], rv[C::CPC];
+            C::template load<R>(t, g.Vh, p, i, j, own);
+            C::template load<R>(p0, g.Vh, p, i, j, pp);
+            C::template load<R>(r, g.Vh, p, i, j, rv);
+#pragma unroll
+            for (int e = 0; e < C::CPC; e++) {
+                const int cix = j * C::CPC + e;
+                cpx<R> res = m4 * own[e] - (R)0.5 * acc[cix];
+                if (cix < 6) res = -res;
+                rv[e] = rv[e] - alpha * (res + sig0 * pp[e]);
+                v[0] += (double)norm2(rv[e]);
+            }
+            C::template store<R>(r, g.Vh, p, i, j, rv);
+        }
+    }
+    grid_reduce<1>(v, rs, ShiftFin{s});
+}
+
+// Elementwise access to a storage word as NR reals.
+template <typename ST> struct Word;
+template <> struct Word<double2> {
+    static constexpr int N = 2;
+    __device__ static void get(const double2 &w, double *o) { o[0] = w.x; o[1] = w.y; }
+    __device__ static double2 put(const double *o) { return make_double2(o[0], o[1]); }
+};
+template <> struct Word<float4> {
+    static constexpr int N = 4;
+    __device__ static void get(const float4 &w, double *o) { o[0] = w.x; o[1] = w.y; o[2] = w.z; o[3] = w.w; }
+    __device__ static float4 put(const double *o) {
+        return make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+    }
+};
+
+// y += sum_l w_l a^l p_l ; p_l = zeta_l r + b^l p_l   (words of ST; nw words per vector).
+// The active shifts are compacted into a list in shared memory and processed four at
+// a time: the four loads of a batch are issued before any store, so each thread keeps
+// four independent memory requests in flight.
+template <typename ST>
+__global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__restrict__ r, ST *__restrict__ y,
+                                                      ST *__restrict__ P, long stride, long nw) {
+    __shared__ double sw[kMaxPoles], sz[kMaxPoles], sb[kMaxPoles];
+    __shared__ int sidx[kMaxPoles];
+    __shared__ int sact, sdone;
+    if (threadIdx.x == 0) {
+        sdone = s->done;
+        int na = 0;
+        if (sdone != 1)
+            for (int l = 0; l < s->n; l++)
+                if (s->active[l]) {
+                    sidx[na] = l;
+                    sw[na] = s->w[l] * s->alpha_l[l];
+                    sz[na] = s->zeta[l];
+                    sb[na] = s->beta_l[l];
+                    na++;
+                }
+        sact = na;
+    }
+    __syncthreads();
+    if (sdone == 1) return;
+    const int na = sact;
+    constexpr int N = Word<ST>::N;
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (long)gridDim.x * blockDim.x) {
+        double rv[N], yv[N];
+        Word<ST>::get(r[k], rv);
+        Word<ST>::get(y[k], yv);
+        for (int a0 = 0; a0 < na; a0 += 4) {
+            ST w[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (a0 + u < na) w[u] = P[(long)sidx[a0 + u] * stride + k];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (a0 + u >= na) break;
+                double pv[N];
+                Word<ST>::get(w[u], pv);
+                const double wl = sw[a0 + u], zl = sz[a0 + u], bl = sb[a0 + u];
+#pragma unroll
+                for (int e = 0; e < N; e++) {
+                    yv[e] += wl * pv[e];
+                    pv[e] = zl * rv[e] + bl * pv[e];
+                }
+                P[(long)sidx[a0 + u] * stride + k] = Word<ST>::put(pv);
+            }
+        }
+        y[k] = Word<ST>::put(yv);
+    }
+}
+
+// Retire shifts marked for a last update, and finish when none is left.
+__global__ void k_ms_retire(MsState *s) {
+    if (s->done == 1) return;
+    for (int l = 0; l < s->n; l++)
+        if (s->active[l] == 2) s->active[l] = 0;
+    if (s->done == 2) s->done = 1;
+}
+
+struct InitFin {
+    MsState *s;
+    __device__ void operator()(const double *v) const {
+        s->bb = v[0];
+        s->rr = v[0];
+        if (v[0] == 0.0) s->done = 1;
+        if (!isfinite(v[0])) {
+            s->status = 1;
+            s->done = 1;
+        }
+    }
+};
+
+// r = y = p_l = b ; ||b||^2
+template <typename ST>
+__global__ void k_ms_init(MsState *s, const ST *__restrict__ b, ST *r, ST *y, ST *P, long stride, long nw,
+                          int n, RedScratch rs) {
+    constexpr int N = Word<ST>::N;
+    double v[1] = {0.0};
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (long)gridDim.x * blockDim.x) {
+        const ST w = b[k];
+        r[k] = w;
+        y[k] = w;
+        for (int l = 0; l < n; l++) P[l * stride + k] = w;
+        double e[N];
+        Word<ST>::get(w, e);
+#pragma unroll
+        for (int q = 0; q < N; q++) v[0] += e[q] * e[q];
+    }
+    grid_reduce<1>(v, rs, InitFin{s});
+}
+
+inline int stream_grid(long n) {
+    long b = (n + kBlock - 1) / kBlock;
+    const long cap = 152L * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename R, typename LT, typename ST>
+cudaError_t ms_iter_t(const Geom &g, const LT *U, R m0, MsState *s, MsVectors<ST> v, RedScratch rs,
+                      cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
+    const int tps = sizeof(R) == 8 ? g.tps64 : g.tps32;
+    const int gs = red_grid(tps == 4 ? 4L * g.V : (long)g.V);
+    cudaError_t e;
+    if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
+    if (tps == 4) k_ms_q4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
+    else k_ms_q<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
+    if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
+    if (tps == 4) k_ms_r4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
+    else k_ms_r<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
+    if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
+    k_ms_shifts<ST><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.y, v.p, v.stride, v.stride);
+    if (ev && (e = cudaEventRecordWithFlags(ev[3], st, ev_flags)) != cudaSuccess) return e;
+    k_ms_retire<<<1, 1, 0, st>>>(s);
+    count_launches(4);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t ms_init_f64(const Geom &g, int n, MsState *s, MsVectors<double2> v, const double2 *b, RedScratch rs,
+                        cudaStream_t st) {
+    k_ms_init<double2><<<red_grid(v.stride), kBlock, 0, st>>>(s, b, v.r, v.y, v.p, v.stride, v.stride, n, rs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t ms_init_f32(const Geom &g, int n, MsState *s, MsVectors<float4> v, const float4 *b, RedScratch rs,
+                        cudaStream_t st) {
+    k_ms_init<float4><<<red_grid(v.stride), kBlock, 0, st>>>(s, b, v.r, v.y, v.p, v.stride, v.stride, n, rs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t ms_iter_f64(const Geom &g, const double2 *U, double m0, MsState *s, MsVectors<double2> v,
+                        RedScratch rs, cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
+    return ms_iter_t<double, double2, double2>(g, U, m0, s, v, rs, st, ev, ev_flags);
+}
+cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, MsVectors<float4> v,
+                        RedScratch rs, cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
+    return ms_iter_t<float, float4, float4>(g, U, m0, s, v, rs, st, ev, ev_flags);
+}
+
+}  // namespace ovl

@@ -1,0 +1,69 @@
+// Deterministic grid reductions: warp shuffles, one shared-memory stage per block,
+// per-block partials in global scratch, and the last block to finish (found with an
+// atomic counter after a memory fence) sums the partials in block order and runs a
+// finalisation functor on thread 0. The summation order depends only on the launch
+// shape, so repeated runs give bit-identical results.
+#pragma once
+#include "internal.h"
+
+namespace ovl {
+
+template <int NV>
+__device__ __forceinline__ void warp_sum(double v[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+}
+
+// Block-wide sum of v[NV]; the result is valid in thread 0. blockDim.x <= 1024.
+template <int NV>
+__device__ __forceinline__ void block_sum(double v[NV]) {
+    __shared__ double sm[NV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    warp_sum<NV>(v);
+    __syncthreads();   // protect sm from a previous use in the same kernel
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) sm[k][warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) v[k] = lane < nw ? sm[k][lane] : 0.0;
+        warp_sum<NV>(v);
+    }
+}
+
+// Reduce v[NV] over the grid; the last block calls fin(total) on thread 0 and
+// resets the counter. Must be reached by every thread of every block.
+template <int NV, typename Fin>
+__device__ __forceinline__ void grid_reduce(double v[NV], RedScratch rs, Fin fin) {
+    __shared__ int is_last;
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) rs.partials[k * kMaxRedBlocks + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned t = atomicAdd(rs.counter, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            s[k] = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+                s[k] += __ldcg(rs.partials + k * kMaxRedBlocks + b);
+        }
+        block_sum<NV>(s);
+        if (threadIdx.x == 0) {
+            fin(s);
+            *rs.counter = 0u;
+        }
+    }
+}
+
+}  // namespace ovl

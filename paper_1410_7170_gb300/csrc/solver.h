@@ -1,0 +1,118 @@
+// Library context and the host-side solver interfaces (internal).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/ovl.h"
+#include "internal.h"
+
+namespace ovl {
+
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    int chunk = 0;
+    bool prof = false;
+};
+
+constexpr int kMaxChunk = 64;
+
+// Event timings of the multishift kernels (instrumentation).
+struct ProfAcc {
+    double q_ms = 0, r_ms = 0, s_ms = 0;
+    long q_n = 0, r_n = 0, s_n = 0;
+    double q_bytes = 0, r_bytes = 0, s_bytes = 0;
+    bool valid = true;
+};
+
+// A Krylov basis workspace: V (m+1 vectors), Z (m vectors, flexible only), w, r.
+template <typename T>
+struct Krylov {
+    T *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
+    int m = 0;
+    bool flexible = false;
+};
+
+struct Ctx {
+    // geometry and operator parameters
+    Geom g{};
+    long n64 = 0;                 // reals per spinor (24 V)
+    double rho_in = 1, mu = 0, rho = 1, m0_ker = -1, m0_prec = 0, sigma_min = 0;
+    ovl_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    // memory
+    std::vector<void *> allocs;
+    size_t bytes_held = 0;
+    void *h_pinned = nullptr;
+    double *h_scal = nullptr;     // pinned scalars (512 doubles)
+    int *h_flag = nullptr;
+    int *h_ms_small = nullptr;
+    MsState *h_ms = nullptr;
+    RedScratch rs{};
+    int *d_flag = nullptr;
+    double *d_scal = nullptr;
+    double *d_md_part = nullptr;  // multi-dot partials
+    double *d_coef = nullptr;     // multi-axpy coefficients
+    // gauge field (12-real links)
+    double2 *U64 = nullptr;
+    float4 *U32 = nullptr;
+    // boundary staging
+    double *io_lex = nullptr;
+    double2 *io_a = nullptr, *io_b = nullptr;
+    // Zolotarev
+    int npole = 0;
+    double lam_min = 0, lam_max = 0, zd0 = 0, zdelta = 0;
+    bool lam_estimated = false;
+    std::vector<double> za, zc;
+    // multishift
+    MsState *ms64_state = nullptr, *ms32_state = nullptr;
+    MsVectors<double2> ms64{};
+    MsVectors<float4> ms32{};
+    GraphSlot graphs[4];
+    // instrumentation
+    bool prof = false;
+    ProfAcc pacc;
+    long launch_mark = 0;
+    cudaEvent_t ev[2][kMaxChunk * 4] = {};
+    bool ev_ready[2] = {false, false};
+    int *d_hist = nullptr;
+    int hist_cap = 0;
+    int *h_hist = nullptr;
+    // Krylov workspaces
+    Krylov<double> kry_outer, kry_wil64;
+    Krylov<float> kry_inner, kry_wil32;
+    float *f_a = nullptr, *f_b = nullptr;   // FP32 conversion buffers
+    void *sap_r32 = nullptr, *sap_r64 = nullptr;   // SAP residual scratch
+    double2 *d_x = nullptr, *d_b = nullptr; // FP64 solve vectors
+    // statistics of the running call
+    long stat_ms64 = 0, stat_ms32 = 0, stat_prec = 0;
+    int stat_inner = 0;
+    float tune_ms[4] = {0, 0, 0, 0};   // stencil ms: fp64 1/4 tps, fp32 1/4 tps
+
+    ~Ctx();
+    ovl_status alloc(void **p, size_t bytes);
+    ovl_status sync();
+    ovl_status fetch(const double *d, int n, double *h);
+    ovl_status norm2_d(const double *x, double *out);
+    ovl_status norm2_f(const float *x, double *out);
+    ovl_status import_vec(const double *src, double2 *dst);
+    ovl_status export_vec(const double2 *src, double *dst);
+    ovl_status ms_setup(MsState *d_state, double tol);
+    template <typename Iter>
+    ovl_status ms_run(MsState *d_state, int which, Iter iter_fn, int *iters_out);
+    ovl_status sign64(const double2 *b, double2 *out, double tol, int mode);
+    ovl_status sign32(const float4 *b, float4 *out, double tol, int mode);
+    ovl_status ensure_ms64();
+    ovl_status ensure_ms32();
+    ovl_status lanczos_bounds(double *lmin, double *lmax);
+    ovl_status sigma_min_estimate(double *smin);
+    ovl_status set_zolotarev();
+    ovl_status autotune();
+};
+
+ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats);
+// Inexact Wilson solve on FP64 even-odd spinors (FP32 inside unless precision == FP64).
+ovl_status wilson_solve_eo(Ctx *c, const double2 *b, double2 *x, double m0, double tol, int *iters);
+
+}  // namespace ovl

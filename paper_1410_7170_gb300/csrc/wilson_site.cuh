@@ -1,0 +1,144 @@
+// One site of the Wilson-Dirac operator, Eq. (Wilson-Dirac) with a = 1:
+//
+//   (D_W psi)(x) = (m0+4) psi(x) - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                                             + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu) ]
+//
+// (1 -+ gamma_mu) = 2 pi^-+_mu has rank 2 (Appendix A, Eq. proj_relations): in the
+// chiral basis gamma_mu = [[0, A_mu], [A_mu^H, 0]] with A_0 = I, A_k = -i sigma_k,
+// (1 - gamma_mu) psi = [h; -A^H h] with h = psi_up - A psi_lo, and
+// (1 + gamma_mu) psi = [h; +A^H h] with h = psi_up + A psi_lo.
+// So each hop projects to a half spinor h (2 spins x 3 colours), multiplies the two
+// colour vectors by the link, and rebuilds the lower two spins with a few sign/i
+// swaps: 2 SU(3) x vector products per hop instead of 4.
+//
+// Antiperiodic time boundary: hops across the x0 boundary carry a factor -1.
+#pragma once
+#include "common.cuh"
+
+namespace ovl {
+
+template <typename R>
+__device__ __forceinline__ void su3_mul(const cpx<R> u[3][3], const cpx<R> h[3], cpx<R> o[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) o[a] = u[a][0] * h[0] + u[a][1] * h[1] + u[a][2] * h[2];
+}
+template <typename R>
+__device__ __forceinline__ void su3_dag_mul(const cpx<R> u[3][3], const cpx<R> h[3], cpx<R> o[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) o[a] = cmul_conj(u[0][a], h[0]) + cmul_conj(u[1][a], h[1]) + cmul_conj(u[2][a], h[2]);
+}
+
+// Forward hop, spin part (1 - gamma_mu): project psi(x+mu) to h0, h1.
+template <typename R>
+__device__ __forceinline__ void proj_fwd(int mu, const cpx<R> s[12], cpx<R> h0[3], cpx<R> h1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const cpx<R> s0 = s[c], s1 = s[3 + c], s2 = s[6 + c], s3 = s[9 + c];
+        switch (mu) {
+            case 0: h0[c] = s0 - s2;          h1[c] = s1 - s3;          break;
+            case 1: h0[c] = s0 + mul_i(s3);   h1[c] = s1 + mul_i(s2);   break;
+            case 2: h0[c] = s0 + s3;          h1[c] = s1 - s2;          break;
+            default: h0[c] = s0 + mul_i(s2);  h1[c] = s1 - mul_i(s3);   break;
+        }
+    }
+}
+// Forward hop: add [a0; a1; -A^H (a0, a1)] into acc.
+template <typename R>
+__device__ __forceinline__ void acc_fwd(int mu, cpx<R> acc[12], const cpx<R> a0[3], const cpx<R> a1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        acc[c] = acc[c] + a0[c];
+        acc[3 + c] = acc[3 + c] + a1[c];
+        switch (mu) {
+            case 0: acc[6 + c] = acc[6 + c] - a0[c];        acc[9 + c] = acc[9 + c] - a1[c];        break;
+            case 1: acc[6 + c] = acc[6 + c] + mul_mi(a1[c]); acc[9 + c] = acc[9 + c] + mul_mi(a0[c]); break;
+            case 2: acc[6 + c] = acc[6 + c] - a1[c];        acc[9 + c] = acc[9 + c] + a0[c];        break;
+            default: acc[6 + c] = acc[6 + c] + mul_mi(a0[c]); acc[9 + c] = acc[9 + c] + mul_i(a1[c]); break;
+        }
+    }
+}
+// Backward hop, spin part (1 + gamma_mu).
+template <typename R>
+__device__ __forceinline__ void proj_bwd(int mu, const cpx<R> s[12], cpx<R> h0[3], cpx<R> h1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const cpx<R> s0 = s[c], s1 = s[3 + c], s2 = s[6 + c], s3 = s[9 + c];
+        switch (mu) {
+            case 0: h0[c] = s0 + s2;          h1[c] = s1 + s3;          break;
+            case 1: h0[c] = s0 + mul_mi(s3);  h1[c] = s1 + mul_mi(s2);  break;
+            case 2: h0[c] = s0 - s3;          h1[c] = s1 + s2;          break;
+            default: h0[c] = s0 + mul_mi(s2); h1[c] = s1 + mul_i(s3);   break;
+        }
+    }
+}
+// Backward hop: add [a0; a1; +A^H (a0, a1)] into acc.
+template <typename R>
+__device__ __forceinline__ void acc_bwd(int mu, cpx<R> acc[12], const cpx<R> a0[3], const cpx<R> a1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        acc[c] = acc[c] + a0[c];
+        acc[3 + c] = acc[3 + c] + a1[c];
+        switch (mu) {
+            case 0: acc[6 + c] = acc[6 + c] + a0[c];        acc[9 + c] = acc[9 + c] + a1[c];        break;
+            case 1: acc[6 + c] = acc[6 + c] + mul_i(a1[c]); acc[9 + c] = acc[9 + c] + mul_i(a0[c]); break;
+            case 2: acc[6 + c] = acc[6 + c] + a1[c];        acc[9 + c] = acc[9 + c] - a0[c];        break;
+            default: acc[6 + c] = acc[6 + c] + mul_i(a0[c]); acc[9 + c] = acc[9 + c] + mul_mi(a1[c]); break;
+        }
+    }
+}
+
+// Hopping sum H(x) = sum_mu [(1-g_mu) U_mu(x) in(x+mu) + (1+g_mu) U_mu(x-mu)^H in(x-mu)]
+// for the site (p, i); `in` is any spinor storage accepted by load_spinor.
+template <typename R, typename LT, typename ST>
+__device__ __forceinline__ void wilson_hop(const Geom &g, const LT *__restrict__ U, ST in, int p, int i,
+                                           cpx<R> acc[12]) {
+    int x[4];
+    eo_coords(g, p, i, x);
+    const int q = 1 - p;
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = cpx<R>{0, 0};
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        {   // forward neighbour x + mu, link U_mu(x) stored at (p, i)
+            int y[4] = {x[0], x[1], x[2], x[3]};
+            y[mu] = (x[mu] + 1 == g.L[mu]) ? 0 : x[mu] + 1;
+            const int j = eo_index(g, y);
+            cpx<R> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
+            load_spinor<R>(in, g.Vh, q, j, s);
+            load_link<R>(U, g.Vh, p, mu, i, u);
+            proj_fwd(mu, s, h0, h1);
+            su3_mul(u, h0, a0);
+            su3_mul(u, h1, a1);
+            if (mu == 0 && g.antiperiodic && x[0] == g.L[0] - 1) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) { a0[c] = -a0[c]; a1[c] = -a1[c]; }
+            }
+            acc_fwd(mu, acc, a0, a1);
+        }
+        {   // backward neighbour x - mu, link U_mu(x - mu)^H stored at (q, j)
+            int y[4] = {x[0], x[1], x[2], x[3]};
+            y[mu] = (x[mu] == 0) ? g.L[mu] - 1 : x[mu] - 1;
+            const int j = eo_index(g, y);
+            cpx<R> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
+            load_spinor<R>(in, g.Vh, q, j, s);
+            load_link<R>(U, g.Vh, q, mu, j, u);
+            proj_bwd(mu, s, h0, h1);
+            su3_dag_mul(u, h0, a0);
+            su3_dag_mul(u, h1, a1);
+            if (mu == 0 && g.antiperiodic && x[0] == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) { a0[c] = -a0[c]; a1[c] = -a1[c]; }
+            }
+            acc_bwd(mu, acc, a0, a1);
+        }
+    }
+}
+
+// res = (m0+4) own - 1/2 hop
+template <typename R>
+__device__ __forceinline__ void wilson_combine(R m4, const cpx<R> own[12], const cpx<R> hop[12], cpx<R> res[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; c++) res[c] = m4 * own[c] - (R)0.5 * hop[c];
+}
+
+}  // namespace ovl

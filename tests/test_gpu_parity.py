@@ -1,0 +1,267 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (FP64 path): 1e-13 relative (max-norm) for the Wilson stencil (only the
+summation order differs), 1e-10 relative (2-norm) per sign / overlap application
+(the stated per-apply bar; the Zolotarev error is below 1e-13 on the interval and the
+multishift CG runs to 1e-12), 1e-8 relative solution error for solves.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense, freefield, sparse, zolotarev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1410_7170_gb300 as ovl  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1410_7170_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def params(**kw):
+    kw.setdefault("lambda_min", 0.05)
+    kw.setdefault("lambda_max", 8.0)
+    return ovl.params_default(**kw)
+
+
+def relmax(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def rel2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("tps", [1, 4])
+@pytest.mark.parametrize("dims,ap,m0", [
+    ((4, 4, 4, 4), True, -1.0),
+    ((2, 6, 6, 10), True, 0.37),      # V = 720: ragged tail of the last block
+    ((4, 2, 8, 6), False, -0.4),
+    ((8, 8, 8, 8), True, -1.0),
+    ((16, 16, 16, 16), True, -1.0),  # the 16^4 workload size
+])
+def test_wilson_apply_matches_oracle(dims, ap, m0, tps):
+    U = synth.gauge_field(dims, 0.5, 100 + sum(dims), stout_steps=1)
+    psi = synth.rhs_gaussian(dims, 200 + sum(dims))
+    ref = sparse.wilson(psi, U, dims, m0, antiperiodic=ap)
+    op = ovl.Overlap(U, dims, 1.0, 0.05, params(antiperiodic=int(ap), stencil_tps=tps))
+    out = torch.empty_like(dev(psi))
+    op.wilson_apply(out, dev(psi), m0)
+    assert relmax(host(out), ref) < 1e-13
+    # host (numpy) buffers through the same entry point
+    out_h = np.empty_like(psi)
+    op.wilson_apply(out_h, psi, m0)
+    assert relmax(out_h, ref) < 1e-13
+    op.close()
+
+
+def test_wilson_free_field_32x32x32x32():
+    """Closed form at the largest 4D workload size: plane waves are eigenvectors."""
+    dims = (32, 32, 32, 32)
+    V = 32 ** 4
+    U = torch.zeros((V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    U[:, :, 0, 0] = 1
+    U[:, :, 1, 1] = 1
+    U[:, :, 2, 2] = 1
+    op = ovl.Overlap(U, dims, 1.0, 0.02, params())
+    for n, br, c in [((3, 1, 4, 1), 1, 0), ((31, 0, 17, 5), -1, 2)]:
+        psi, lam0 = freefield.plane_wave_eigvec(dims, n, br, c)
+        x = dev(psi)
+        out = torch.empty_like(x)
+        op.wilson_apply(out, x, -1.0)
+        expect = (lam0 - 1.0) * x
+        assert (out - expect).abs().max().item() < 1e-13
+    op.close()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 1001)
+    rho = dense.rho_from_mu(0.05, -1.0)
+    DN, S, w = dense.overlap_dense(U, dims, rho, -1.0)
+    return dims, U, rho, DN, S, np.abs(w)
+
+
+@pytest.mark.parametrize("tps", [1, 4])
+def test_sign_apply_matches_dense_sign(c1, tps):
+    dims, U, rho, DN, S, aw = c1
+    p = params(lambda_min=0.98 * aw.min(), lambda_max=1.02 * aw.max(), n_poles=20, stencil_tps=tps)
+    op = ovl.Overlap(U, dims, 1.0, 0.05, p)
+    b = synth.rhs_gaussian(dims, 2001)
+    out = torch.empty_like(dev(b))
+    op.sign_apply(out, dev(b), 1e-12)
+    ref = (S @ b.reshape(-1)).reshape(b.shape)
+    assert rel2(host(out), ref) < 1e-10
+    out2 = torch.empty_like(out)
+    op.ovl_apply(out2, dev(b), 1e-12)
+    ref2 = (DN @ b.reshape(-1)).reshape(b.shape)
+    assert rel2(host(out2), ref2) < 1e-10
+    op.close()
+
+
+def test_lanczos_interval_encloses_spectrum(c1):
+    dims, U, rho, DN, S, aw = c1
+    op = ovl.Overlap(U, dims, 1.0, 0.05, ovl.params_default())
+    info = op.info()
+    assert info["lambda_min"] <= aw.min() and info["lambda_max"] >= aw.max()
+    assert info["lambda_min"] > 0.5 * aw.min() and info["lambda_max"] < 1.5 * aw.max()
+    assert abs(info["rho"] - rho) < 1e-15
+    # with the estimated interval the sign still meets the per-apply bar
+    b = synth.rhs_gaussian(dims, 2002)
+    out = torch.empty_like(dev(b))
+    op.sign_apply(out, dev(b), 1e-12)
+    ref = (S @ b.reshape(-1)).reshape(b.shape)
+    assert rel2(host(out), ref) < 1e-10
+    op.close()
+
+
+def test_sign_apply_matches_sparse_oracle_8x8x8x8():
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_field(dims, 0.5, 1102, stout_steps=3)
+    lmin, lmax = 0.3, 7.0
+    p = params(lambda_min=lmin, lambda_max=lmax, n_poles=16)
+    op = ovl.Overlap(U, dims, 1.0, 0.01, p)
+    b = synth.rhs_gaussian(dims, 2102)
+    out = torch.empty_like(dev(b))
+    op.sign_apply(out, dev(b), 1e-12)
+    co = zolotarev.zolotarev_coefficients(lmin / lmax, 16)
+    ref, _ = sparse.sign_zolo(b, U, dims, -1.0, lmin, co, 1e-13)
+    assert rel2(host(out), ref) < 1e-10
+    op.close()
+
+
+def test_sign_squares_to_identity_16x16x16x16():
+    """Sec. 2: sign(Q)^2 = I, at the 16^4 workload size with the estimated interval."""
+    dims = (16, 16, 16, 16)
+    U = synth.gauge_field(dims, 0.5, 1002, stout_steps=3)
+    op = ovl.Overlap(U, dims, 1.0, 0.01, ovl.params_default())
+    b = dev(synth.rhs_gaussian(dims, 2003))
+    s1 = torch.empty_like(b)
+    s2 = torch.empty_like(b)
+    op.sign_apply(s1, b, 1e-11)
+    op.sign_apply(s2, s1, 1e-11)
+    assert ((s2 - b).norm() / b.norm()).item() < 1e-9
+    assert abs((s1.norm() / b.norm()).item() - 1.0) < 1e-9
+    op.close()
+
+
+def test_gmres_solve_matches_dense_lu(c1):
+    """Config 1: 4^4, unpreconditioned GMRES(100) in FP64 against the dense LU solution."""
+    dims, U, rho, DN, S, aw = c1
+    p = params(lambda_min=0.98 * aw.min(), lambda_max=1.02 * aw.max(), precond=ovl.OVL_PREC_NONE)
+    op = ovl.Overlap(U, dims, 1.0, 0.05, p)
+    b = synth.rhs_gaussian(dims, 2001)
+    x = torch.zeros_like(dev(b))
+    st, stats = op.ovl_solve(x, dev(b), 1, 1e-11)
+    ref = dense.overlap_solve_dense(DN, b)
+    assert rel2(host(x), ref) < 1e-8
+    r = b.reshape(-1) - DN @ host(x).reshape(-1)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-10
+    assert stats["outer_iters"] > 0 and stats["ms_iters_fp64"] > 0
+    op.close()
+
+
+@pytest.mark.parametrize("precond,precision,tps", [
+    (ovl.OVL_PREC_WILSON, ovl.OVL_FP64, 1),
+    (ovl.OVL_PREC_WILSON, ovl.OVL_MIXED_FP32, 4),
+    (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_FP32, 1),
+    (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_FP32, 4),
+])
+def test_preconditioned_solves_match_dense_lu(c1, precond, precision, tps):
+    dims, U, rho, DN, S, aw = c1
+    p = params(lambda_min=0.98 * aw.min(), lambda_max=1.02 * aw.max(), precond=precond, precision=precision,
+               sap_block=(2, 2, 2, 2), stencil_tps=tps)
+    op = ovl.Overlap(U, dims, 1.0, 0.05, p)
+    b = synth.rhs_gaussian(dims, 2001)
+    x = torch.zeros_like(dev(b))
+    st, stats = op.ovl_solve(x, dev(b), 1, 1e-11)
+    ref = dense.overlap_solve_dense(DN, b)
+    assert rel2(host(x), ref) < 1e-8
+    op.close()
+
+
+def test_multiple_rhs_and_initial_guess(c1):
+    dims, U, rho, DN, S, aw = c1
+    p = params(lambda_min=0.98 * aw.min(), lambda_max=1.02 * aw.max())
+    op = ovl.Overlap(U, dims, 1.0, 0.05, p)
+    b = synth.rhs_gaussian(dims, 2005, n_rhs=3)
+    x = torch.zeros_like(dev(b))
+    op.ovl_solve(x, dev(b), 3, 1e-11)
+    for k in range(3):
+        ref = dense.overlap_solve_dense(DN, b[k])
+        assert rel2(host(x[k]), ref) < 1e-8
+    # restarting from the solution converges at once
+    st, stats = op.ovl_solve(x, dev(b), 3, 1e-9)
+    assert stats["outer_iters"] == 0
+    op.close()
+
+
+def test_errors_are_reported_not_raised_on_device():
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 5)
+    bad = U.copy()
+    bad[3, 1] *= 1.01
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.Overlap(bad, dims, 1.0, 0.05, params())
+    assert e.value.status == ovl.OVL_EINVAL
+    with pytest.raises(ovl.OvlError):
+        ovl.Overlap(U, (4, 4, 4, 3), 1.0, 0.05, params())
+    op = ovl.Overlap(U, dims, 1.0, 0.05, params())
+    b = synth.rhs_gaussian(dims, 6)
+    b[7, 2, 1] = np.nan
+    out = np.empty_like(b)
+    with pytest.raises(ovl.OvlError) as e:
+        op.wilson_apply(out, b, -1.0)
+    assert e.value.status == ovl.OVL_EINVAL
+    with pytest.raises(ovl.OvlError):
+        op.sign_apply(out, synth.rhs_gaussian(dims, 7), 0.0)
+    # the context is still usable after an argument error
+    b2 = synth.rhs_gaussian(dims, 8)
+    op.wilson_apply(out, b2, -1.0)
+    assert relmax(out, sparse.wilson(b2, U, dims, -1.0)) < 1e-13
+    op.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(ovl.OVL_MIXED_FP32, 1e-5), (ovl.OVL_FP64, 1e-10)])
+def test_wilson_solve_residual_and_sap_quality(precision, tol):
+    """The inexact Wilson solve (Sec. 5.1 preconditioner) reaches its tolerance, checked
+    with the oracle's D_W; stronger Schwarz smoothing needs fewer outer iterations."""
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_field(dims, 0.5, 1202, stout_steps=3)
+    b = synth.rhs_gaussian(dims, 2202)
+    m0 = -0.3
+    its = []
+    for cyc, mr in [(1, 1), (2, 4)]:
+        op = ovl.Overlap(U, dims, 1.0, 0.01, params(precision=precision, sap_cycles=cyc, sap_mr_iters=mr,
+                                                    prec_max_iter=400, prec_restart=32))
+        x = np.zeros_like(b)
+        its.append(op.wilson_solve(x, b, m0, tol))
+        r = b - sparse.wilson(x, U, dims, m0)
+        assert np.linalg.norm(r) / np.linalg.norm(b) < tol * 1.5
+        op.close()
+    assert its[1] < its[0]
+
+
+def test_autotuner_reports_a_choice():
+    dims = (16, 16, 16, 16)
+    U = synth.gauge_field(dims, 0.5, 7, stout_steps=0)
+    op = ovl.Overlap(U, dims, 1.0, 0.01, params())
+    t = op.tuning()
+    assert t["tps64"] in (1, 4) and t["tps32"] in (1, 4)
+    assert all(m > 0 for m in t["ms"])
+    op.close()

@@ -1,0 +1,74 @@
+"""Host-only checks of the C-ABI library: it builds, loads without a GPU,
+exports every function include/ovl.h declares, and its host-side Zolotarev
+coefficients (own AGM/Landen elliptic functions) match the oracle's
+(scipy elliptic functions, grid-centred scale)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1410_7170_gb300 as ovl
+from oracle import zolotarev
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1410_7170_gb300 import build
+    build.build()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(?:ovl_status|const char \*)\s*(\w+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol():
+    decl = _declared()
+    assert {"ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve", "ovl_destroy"} <= decl
+    out = subprocess.run(["nm", "-D", "--defined-only", ovl.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\s[TW]\s(\w+)$", out, flags=re.M))
+    assert decl <= exported, decl - exported
+    L = ovl.lib()
+    for name in decl:
+        assert hasattr(L, name)
+
+
+def test_params_default_are_paper_values():
+    """Table 2 / Table 3 defaults (see tests/golden/paper_values.json)."""
+    import json
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_values.json")))
+    p = ovl.params_default()
+    assert p.tol_outer == gold["table2_eps_outer"]["value"]
+    assert p.restart == gold["table2_restart"]["value"]
+    assert p.relax_factor == gold["table2_relaxation_factor"]["value"]
+    assert p.eps_prec == gold["table2_eps_prec"]["value"]
+    assert p.eps_inner == gold["table3_eps_inner_prec"]["value"]
+    assert p.restart_inner == gold["table3_restart_inner"]["value"]
+
+
+@pytest.mark.parametrize("k,n", [(0.05, 20), (0.01, 20), (0.1, 5), (0.2, 3), (0.003, 30)])
+def test_host_zolotarev_matches_oracle(k, n):
+    d0, a, c, delta = ovl.ovl_zolotarev(k, n)
+    co = zolotarev.zolotarev_coefficients(k, n)
+    assert np.allclose(c, co["c_den"], rtol=1e-11)
+    assert np.allclose(a, co["a"], rtol=1e-9, atol=1e-14 * np.abs(co["a"]).max())
+    assert abs(d0 - co["d0"]) < 1e-12 * co["d0"] + co["delta"]
+    lam = np.exp(np.linspace(0, np.log(1 / k), 20001))
+    approx = d0 * lam * (1 + sum(ai / (lam ** 2 + ci) for ai, ci in zip(a, c)))
+    assert np.max(np.abs(1 - approx)) <= max(delta, 1e-14) * 1.01 + 1e-14
+
+
+def test_zolotarev_rejects_bad_interval():
+    with pytest.raises(ovl.OvlError):
+        ovl.ovl_zolotarev(1.5, 10)
+    with pytest.raises(ovl.OvlError):
+        ovl.ovl_zolotarev(0.1, 0)
