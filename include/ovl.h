@@ -177,13 +177,16 @@ ovl_status ovl_zolotarev(double k, int n, double *d0, double *a, double *c, doub
  * 144, shift update 72 + 48 per updated shift) are accumulated from the launches
  * that do the work. Timings cost one event pair per kernel. */
 typedef struct {
+    double ms;              /* summed event time of the kernel class */
+    long launches;
+    double bytes;           /* summed algorithmic bytes */
+    double flops;           /* summed algorithmic flops (stencils: 1368 per site) */
+} ovl_prof_kernel;
+
+typedef struct {
     long launches;          /* kernels launched by the library since the last reset (all contexts) */
-    double stencil_ms;      /* multishift stencil kernels (Q p and residual update): total time */
-    long stencil_launches;
-    double stencil_bytes;   /* their algorithmic bytes */
-    double shifts_ms;       /* multishift shift-update kernel */
-    long shifts_launches;
-    double shifts_bytes;
+    ovl_prof_kernel k[4];   /* 0: FP64 multishift stencils, 1: FP64 shift updates,
+                               2: FP32 multishift stencils, 3: FP32 shift updates */
     int valid;              /* 1 if every event timing could be read */
 } ovl_prof;
 

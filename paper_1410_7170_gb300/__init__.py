@@ -54,15 +54,22 @@ class ovl_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ovl_prof_kernel(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_long), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
+
+PROF_KERNELS = ["ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_f32"]
+
+
 class ovl_prof(ctypes.Structure):
-    _fields_ = [
-        ("launches", ctypes.c_long), ("stencil_ms", ctypes.c_double), ("stencil_launches", ctypes.c_long),
-        ("stencil_bytes", ctypes.c_double), ("shifts_ms", ctypes.c_double), ("shifts_launches", ctypes.c_long),
-        ("shifts_bytes", ctypes.c_double), ("valid", ctypes.c_int),
-    ]
+    _fields_ = [("launches", ctypes.c_long), ("k", ovl_prof_kernel * 4), ("valid", ctypes.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {"launches": self.launches, "valid": self.valid}
+        for name, k in zip(PROF_KERNELS, self.k):
+            d[name] = {"ms": k.ms, "launches": k.launches, "bytes": k.bytes, "flops": k.flops}
+        return d
 
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",

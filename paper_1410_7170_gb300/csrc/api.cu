@@ -107,6 +107,7 @@ static bool is_device_ptr(const void *p) {
     do {                                                                           \
         cudaError_t e_ = (expr);                                                   \
         if (e_ != cudaSuccess) {                                                   \
+            cudaGetLastError();                                                    \
             c->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #expr; \
             return OVL_ECUDA;                                                      \
         }                                                                          \
@@ -289,16 +290,17 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, Iter iter_fn, int *iters_out
                     cudaEventElapsedTime(&b, ev[which][4 * k + 1], ev[which][4 * k + 2]) != cudaSuccess ||
                     cudaEventElapsedTime(&d, ev[which][4 * k + 2], ev[which][4 * k + 3]) != cudaSuccess) {
                     cudaGetLastError();
-                    pacc.valid = false;
+                    pacc[which].valid = false;
                     continue;
                 }
-                pacc.q_ms += a; pacc.r_ms += b; pacc.s_ms += d;
-                pacc.q_n++; pacc.r_n++; pacc.s_n++;
+                ProfAcc &pa = pacc[which];
+                pa.q_ms += a; pa.r_ms += b; pa.s_ms += d;
+                pa.q_n++; pa.r_n++; pa.s_n++;
                 // algorithmic reals per site: Q p: p, 4 links x 12, t; residual: t, links, p, r in/out;
                 // shifts: r, y in/out, each updated p_l in/out
-                pacc.q_bytes += 96.0 * V * rbytes;
-                pacc.r_bytes += 144.0 * V * rbytes;
-                pacc.s_bytes += (72.0 + 48.0 * h_hist[k]) * V * rbytes;
+                pa.q_bytes += 96.0 * V * rbytes;
+                pa.r_bytes += 144.0 * V * rbytes;
+                pa.s_bytes += (72.0 + 48.0 * h_hist[k]) * V * rbytes;
             }
         }
         iter_before = iter;
@@ -515,7 +517,11 @@ ovl_status Ctx::sigma_min_estimate(double *smin) {
 #include <mutex>
 #include <tuple>
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+struct TuneEntry {
+    int tps64, tps32;
+    float ms[4];
+};
+static std::map<std::tuple<int, int, int, int>, TuneEntry> g_tune_cache;
 
 ovl_status Ctx::autotune() {
     Ctx *c = this;
@@ -524,8 +530,9 @@ ovl_status Ctx::autotune() {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            g.tps64 = it->second.first;
-            g.tps32 = it->second.second;
+            g.tps64 = it->second.tps64;
+            g.tps32 = it->second.tps32;
+            for (int k = 0; k < 4; k++) tune_ms[k] = it->second.ms[k];
             return OVL_OK;
         }
     }
@@ -564,7 +571,8 @@ ovl_status Ctx::autotune() {
     tune_ms[3] = best[1][1] / reps;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = std::make_pair(g.tps64, g.tps32);
+        TuneEntry te{g.tps64, g.tps32, {tune_ms[0], tune_ms[1], tune_ms[2], tune_ms[3]}};
+        g_tune_cache[key] = te;
     }
     cudaFree(buf);
     allocs.erase(std::find(allocs.begin(), allocs.end(), buf));
@@ -816,16 +824,25 @@ extern "C" ovl_status ovl_prof_enable(ovl_ctx *ctx, int on) {
 extern "C" ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !out) return OVL_EINVAL;
+    memset(out, 0, sizeof(*out));
     out->launches = launches_total() - c->launch_mark;
-    out->stencil_ms = c->pacc.q_ms + c->pacc.r_ms;
-    out->stencil_launches = c->pacc.q_n + c->pacc.r_n;
-    out->stencil_bytes = c->pacc.q_bytes + c->pacc.r_bytes;
-    out->shifts_ms = c->pacc.s_ms;
-    out->shifts_launches = c->pacc.s_n;
-    out->shifts_bytes = c->pacc.s_bytes;
-    out->valid = c->pacc.valid ? 1 : 0;
+    out->valid = 1;
+    const double V = (double)c->g.V;
+    for (int w = 0; w < 2; w++) {
+        const ProfAcc &pa = c->pacc[w];
+        ovl_prof_kernel &st = out->k[2 * w], &sh = out->k[2 * w + 1];
+        st.ms = pa.q_ms + pa.r_ms;
+        st.launches = pa.q_n + pa.r_n;
+        st.bytes = pa.q_bytes + pa.r_bytes;
+        st.flops = 1368.0 * V * (double)st.launches;
+        sh.ms = pa.s_ms;
+        sh.launches = pa.s_n;
+        sh.bytes = pa.s_bytes;
+        if (!pa.valid) out->valid = 0;
+    }
     if (reset) {
-        c->pacc = ProfAcc();
+        c->pacc[0] = ProfAcc();
+        c->pacc[1] = ProfAcc();
         c->launch_mark = launches_total();
     }
     return OVL_OK;

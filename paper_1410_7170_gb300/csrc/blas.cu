@@ -17,26 +17,28 @@ struct StoreFin2 {
     __device__ void operator()(const double *s) const { res[0] = s[0]; res[1] = s[1]; }
 };
 
+// Per-thread partial sums are kept in the vector's own precision T (a grid-stride
+// thread sees only a few elements); blocks and the grid are summed in FP64.
 template <typename T>
 __global__ void k_norm2(const T *__restrict__ x, long n, RedScratch rs, double *res) {
-    double v[1] = {0.0};
-    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-        const double a = (double)x[k];
-        v[0] += a * a;
-    }
+    T a = 0;
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        a += x[k] * x[k];
+    double v[1] = {(double)a};
     grid_reduce<1>(v, rs, StoreFin1{res});
 }
 
 // <x, y> = sum conj(x) y over complex numbers stored as (re, im) pairs
 template <typename T>
 __global__ void k_cdot(const T *__restrict__ x, const T *__restrict__ y, long nc, RedScratch rs, double *res) {
-    double v[2] = {0.0, 0.0};
+    T a = 0, b = 0;
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += (long)gridDim.x * blockDim.x) {
-        const double xr = (double)x[2 * k], xi = (double)x[2 * k + 1];
-        const double yr = (double)y[2 * k], yi = (double)y[2 * k + 1];
-        v[0] += xr * yr + xi * yi;
-        v[1] += xr * yi - xi * yr;
+        const T xr = x[2 * k], xi = x[2 * k + 1];
+        const T yr = y[2 * k], yi = y[2 * k + 1];
+        a += xr * yr + xi * yi;
+        b += xr * yi - xi * yr;
     }
+    double v[2] = {(double)a, (double)b};
     grid_reduce<2>(v, rs, StoreFin2{res});
 }
 
@@ -61,13 +63,14 @@ template <typename T>
 __global__ void k_multidot_part(const T *__restrict__ base, long stride, const T *__restrict__ w, long nc,
                                 double *partials) {
     const T *v = base + (long)blockIdx.y * stride;
-    double s[2] = {0.0, 0.0};
+    T a = 0, b = 0;
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += (long)gridDim.x * blockDim.x) {
-        const double vr = (double)v[2 * k], vi = (double)v[2 * k + 1];
-        const double wr = (double)w[2 * k], wi = (double)w[2 * k + 1];
-        s[0] += vr * wr + vi * wi;
-        s[1] += vr * wi - vi * wr;
+        const T vr = v[2 * k], vi = v[2 * k + 1];
+        const T wr = w[2 * k], wi = w[2 * k + 1];
+        a += vr * wr + vi * wi;
+        b += vr * wi - vi * wr;
     }
+    double s[2] = {(double)a, (double)b};
     block_sum<2>(s);
     if (threadIdx.x == 0) {
         partials[((long)blockIdx.y * gridDim.x + blockIdx.x) * 2] = s[0];
@@ -90,19 +93,19 @@ __global__ void k_multidot_sum(const double *partials, int nb, double *out) {
 template <typename T>
 __global__ void k_multiaxpy(const T *__restrict__ base, long stride, int m, const double *__restrict__ c,
                             T *__restrict__ w, long nc) {
-    __shared__ double cs[2 * 128];
-    for (int k = threadIdx.x; k < 2 * m; k += blockDim.x) cs[k] = c[k];
+    __shared__ T cs[2 * 128];   // coefficients in the vectors' precision
+    for (int k = threadIdx.x; k < 2 * m; k += blockDim.x) cs[k] = (T)c[k];
     __syncthreads();
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += (long)gridDim.x * blockDim.x) {
-        double ar = (double)w[2 * k], ai = (double)w[2 * k + 1];
+        T ar = w[2 * k], ai = w[2 * k + 1];
         for (int j = 0; j < m; j++) {
             const T *v = base + (long)j * stride;
-            const double vr = (double)v[2 * k], vi = (double)v[2 * k + 1];
+            const T vr = v[2 * k], vi = v[2 * k + 1];
             ar += cs[2 * j] * vr - cs[2 * j + 1] * vi;
             ai += cs[2 * j] * vi + cs[2 * j + 1] * vr;
         }
-        w[2 * k] = (T)ar;
-        w[2 * k + 1] = (T)ai;
+        w[2 * k] = ar;
+        w[2 * k + 1] = ai;
     }
 }
 

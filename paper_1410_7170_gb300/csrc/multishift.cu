@@ -110,11 +110,14 @@ __global__ void __launch_bounds__(kBlock) k_ms_q(Geom g, const LT *__restrict__ 
         wilson_combine<R>(m4, own, hop, res);
         apply_g5(res);
         store_spinor<R>(t, g.Vh, p, i, res);
+        R a0 = 0, a1 = 0;   // per-site sums in the arithmetic type, across sites in FP64
 #pragma unroll
         for (int c = 0; c < 12; c++) {
-            v[0] += (double)norm2(res[c]);
-            v[1] += (double)norm2(own[c]);
+            a0 += norm2(res[c]);
+            a1 += norm2(own[c]);
         }
+        v[0] += (double)a0;
+        v[1] += (double)a1;
     }
     grid_reduce<2>(v, rs, AlphaFin{s});
 }
@@ -136,11 +139,13 @@ __global__ void __launch_bounds__(kBlock) k_ms_r(Geom g, const LT *__restrict__ 
         apply_g5(res);
         load_spinor<R>(p0, g.Vh, p, i, pp);
         load_spinor<R>(r, g.Vh, p, i, rv);
+        R a0 = 0;
 #pragma unroll
         for (int c = 0; c < 12; c++) {
             rv[c] = rv[c] - alpha * (res[c] + sig0 * pp[c]);
-            v[0] += (double)norm2(rv[c]);
+            a0 += norm2(rv[c]);
         }
+        v[0] += (double)a0;
         store_spinor<R>(r, g.Vh, p, i, rv);
     }
     grid_reduce<1>(v, rs, ShiftFin{s});
@@ -169,14 +174,17 @@ __global__ void __launch_bounds__(kBlock) k_ms_q4(Geom g, const LT *__restrict__
             if ((j & 3) != q) continue;
             cpx<R> own[C::CPC], res[C::CPC];
             C::template load<R>(p0, g.Vh, p, i, j, own);
+            R a0 = 0, a1 = 0;
 #pragma unroll
             for (int e = 0; e < C::CPC; e++) {
                 const int cix = j * C::CPC + e;
                 res[e] = m4 * own[e] - (R)0.5 * acc[cix];
                 if (cix < 6) res[e] = -res[e];
-                v[0] += (double)norm2(res[e]);
-                v[1] += (double)norm2(own[e]);
+                a0 += norm2(res[e]);
+                a1 += norm2(own[e]);
             }
+            v[0] += (double)a0;
+            v[1] += (double)a1;
             C::template store<R>(t, g.Vh, p, i, j, res);
         }
     }
@@ -209,13 +217,15 @@ __global__ void __launch_bounds__(kBlock) k_ms_r4(Geom g, const LT *__restrict__
             C::template load<R>(p0, g.Vh, p, i, j, pp);
             C::template load<R>(r, g.Vh, p, i, j, rv);
 #pragma unroll
+            R a0 = 0;
             for (int e = 0; e < C::CPC; e++) {
                 const int cix = j * C::CPC + e;
                 cpx<R> res = m4 * own[e] - (R)0.5 * acc[cix];
                 if (cix < 6) res = -res;
                 rv[e] = rv[e] - alpha * (res + sig0 * pp[e]);
-                v[0] += (double)norm2(rv[e]);
+                a0 += norm2(rv[e]);
             }
+            v[0] += (double)a0;
             C::template store<R>(r, g.Vh, p, i, j, rv);
         }
     }
@@ -224,17 +234,18 @@ __global__ void __launch_bounds__(kBlock) k_ms_r4(Geom g, const LT *__restrict__
 
 // Elementwise access to a storage word as NR reals.
 template <typename ST> struct Word;
+// A = arithmetic type of the elementwise updates (the storage precision).
 template <> struct Word<double2> {
     static constexpr int N = 2;
-    __device__ static void get(const double2 &w, double *o) { o[0] = w.x; o[1] = w.y; }
-    __device__ static double2 put(const double *o) { return make_double2(o[0], o[1]); }
+    using A = double;
+    __device__ static void get(const double2 &w, A *o) { o[0] = w.x; o[1] = w.y; }
+    __device__ static double2 put(const A *o) { return make_double2(o[0], o[1]); }
 };
 template <> struct Word<float4> {
     static constexpr int N = 4;
-    __device__ static void get(const float4 &w, double *o) { o[0] = w.x; o[1] = w.y; o[2] = w.z; o[3] = w.w; }
-    __device__ static float4 put(const double *o) {
-        return make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
-    }
+    using A = float;
+    __device__ static void get(const float4 &w, A *o) { o[0] = w.x; o[1] = w.y; o[2] = w.z; o[3] = w.w; }
+    __device__ static float4 put(const A *o) { return make_float4(o[0], o[1], o[2], o[3]); }
 };
 
 // y += sum_l w_l a^l p_l ; p_l = zeta_l r + b^l p_l   (words of ST; nw words per vector).
@@ -244,7 +255,8 @@ template <> struct Word<float4> {
 template <typename ST>
 __global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__restrict__ r, ST *__restrict__ y,
                                                       ST *__restrict__ P, long stride, long nw) {
-    __shared__ double sw[kMaxPoles], sz[kMaxPoles], sb[kMaxPoles];
+    using A = typename Word<ST>::A;
+    __shared__ A sw[kMaxPoles], sz[kMaxPoles], sb[kMaxPoles];
     __shared__ int sidx[kMaxPoles];
     __shared__ int sact, sdone;
     if (threadIdx.x == 0) {
@@ -254,9 +266,9 @@ __global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__re
             for (int l = 0; l < s->n; l++)
                 if (s->active[l]) {
                     sidx[na] = l;
-                    sw[na] = s->w[l] * s->alpha_l[l];
-                    sz[na] = s->zeta[l];
-                    sb[na] = s->beta_l[l];
+                    sw[na] = (A)(s->w[l] * s->alpha_l[l]);
+                    sz[na] = (A)s->zeta[l];
+                    sb[na] = (A)s->beta_l[l];
                     na++;
                 }
         sact = na;
@@ -266,7 +278,7 @@ __global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__re
     const int na = sact;
     constexpr int N = Word<ST>::N;
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (long)gridDim.x * blockDim.x) {
-        double rv[N], yv[N];
+        A rv[N], yv[N];
         Word<ST>::get(r[k], rv);
         Word<ST>::get(y[k], yv);
         for (int a0 = 0; a0 < na; a0 += 4) {
@@ -277,9 +289,9 @@ __global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__re
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 if (a0 + u >= na) break;
-                double pv[N];
+                A pv[N];
                 Word<ST>::get(w[u], pv);
-                const double wl = sw[a0 + u], zl = sz[a0 + u], bl = sb[a0 + u];
+                const A wl = sw[a0 + u], zl = sz[a0 + u], bl = sb[a0 + u];
 #pragma unroll
                 for (int e = 0; e < N; e++) {
                     yv[e] += wl * pv[e];
@@ -324,10 +336,11 @@ __global__ void k_ms_init(MsState *s, const ST *__restrict__ b, ST *r, ST *y, ST
         r[k] = w;
         y[k] = w;
         for (int l = 0; l < n; l++) P[l * stride + k] = w;
-        double e[N];
+        typename Word<ST>::A e[N], a = 0;
         Word<ST>::get(w, e);
 #pragma unroll
-        for (int q = 0; q < N; q++) v[0] += e[q] * e[q];
+        for (int q = 0; q < N; q++) a += e[q] * e[q];
+        v[0] += (double)a;
     }
     grid_reduce<1>(v, rs, InitFin{s});
 }

@@ -118,7 +118,9 @@ __global__ void k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const 
     if (((B[0] + B[1] + B[2] + B[3]) & 1) != colour) return;   // uniform over the CTA
     R *s = reinterpret_cast<R *>(smem_raw);
     R *u = s + 24 * nb;
-    const int t = threadIdx.x;
+    // the CTA is padded to whole warps; threads t >= nb hold no site but join the reductions
+    const bool act = threadIdx.x < nb;
+    const int t = act ? threadIdx.x : 0;
     int l[4], rr = t;
     l[3] = rr % sg.b[3]; rr /= sg.b[3];
     l[2] = rr % sg.b[2]; rr /= sg.b[2];
@@ -131,7 +133,7 @@ __global__ void k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const 
     const int i = eo_index(g, xg);
     // links U_mu(x) of the block sites (forward links; backward ones are the neighbours')
 #pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
+    for (int mu = 0; mu < 4 && act; mu++) {
         cpx<R> m[3][3];
         load_link<R>(U, g.Vh, p, mu, i, m);
         R *b = u + (size_t)mu * 18 * nb + t;
@@ -144,22 +146,28 @@ __global__ void k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const 
             }
     }
     cpx<R> res[12], e[12], q[12];
-    load_spinor<R>(r, g.Vh, p, i, res);
 #pragma unroll
-    for (int c = 0; c < 12; c++) e[c] = cpx<R>{0, 0};
+    for (int c = 0; c < 12; c++) {
+        e[c] = cpx<R>{0, 0};
+        res[c] = cpx<R>{0, 0};
+        q[c] = cpx<R>{0, 0};
+    }
+    if (act) load_spinor<R>(r, g.Vh, p, i, res);
     for (int it = 0; it < mr_iters; it++) {
-        sm_store_sp(s, nb, t, res);
+        if (act) sm_store_sp(s, nb, t, res);
         __syncthreads();
-        block_apply<R>(s, u, nb, t, l, sg.b, sg.stride, m4, q);
-        double v[3] = {0.0, 0.0, 0.0};
+        if (act) block_apply<R>(s, u, nb, t, l, sg.b, sg.stride, m4, q);
+        R a0 = 0, a1 = 0, a2 = 0;   // per-site sums in the arithmetic type, block sums in FP64
 #pragma unroll
         for (int c = 0; c < 12; c++) {
-            v[0] += (double)(q[c].re * res[c].re + q[c].im * res[c].im);   // Re <q, s>
-            v[1] += (double)(q[c].re * res[c].im - q[c].im * res[c].re);   // Im <q, s>
-            v[2] += (double)norm2(q[c]);
+            a0 += q[c].re * res[c].re + q[c].im * res[c].im;   // Re <q, s>
+            a1 += q[c].re * res[c].im - q[c].im * res[c].re;   // Im <q, s>
+            a2 += norm2(q[c]);
         }
+        double v[3] = {(double)a0, (double)a1, (double)a2};
         block_sum_sh<R>(v, sh);
-        if (!(v[2] > 0.0)) break;
+        if (!(v[2] > 0.0)) break;   // uniform: every thread holds the block sums
+        __syncthreads();            // smem s is rewritten at the top of the next step
         const cpx<R> alpha = cpx<R>{(R)(v[0] / v[2]), (R)(v[1] / v[2])};
 #pragma unroll
         for (int c = 0; c < 12; c++) {
@@ -167,6 +175,7 @@ __global__ void k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const 
             res[c] = res[c] - alpha * q[c];
         }
     }
+    if (!act) return;
     cpx<R> xv[12];
     load_spinor<R>(x, g.Vh, p, i, xv);
 #pragma unroll
@@ -182,13 +191,16 @@ static cudaError_t sap_t(const Geom &g, const SapGeom &sg, const LT *U, const ST
                          cudaError_t (*wil)(const Geom &, const LT *, const ST *, ST *, R, int, R, const ST *, R,
                                             cudaStream_t)) {
     const size_t smem = (size_t)sg.nb * (24 + 4 * 18) * sizeof(R);
-    static bool attr_set[2] = {false, false};
+    static size_t attr_set[2] = {0, 0};   // dynamic shared memory granted so far, per precision
     const int which = sizeof(R) == 8;
-    if (!attr_set[which]) {
+    if (smem > 48 * 1024 && smem > attr_set[which]) {
         cudaError_t e = cudaFuncSetAttribute(k_sap_block<R, LT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(227 * 1024));
-        if (e != cudaSuccess) return e;
-        attr_set[which] = true;
+                                             (int)smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        attr_set[which] = smem;
     }
     cudaError_t e = cudaMemsetAsync(x, 0, (size_t)g.V * 24 * sizeof(R), st);
     if (e != cudaSuccess) return e;
@@ -202,7 +214,8 @@ static cudaError_t sap_t(const Geom &g, const SapGeom &sg, const LT *U, const ST
                 if ((e = wil(g, U, x, r, m0, 0, (R)-1, v, (R)1, st)) != cudaSuccess) return e;
                 res = r;
             }
-            k_sap_block<R, LT, ST><<<nblocks, sg.nb, smem, st>>>(g, sg, U, res, x, m0 + (R)4, colour, mr_iters);
+            k_sap_block<R, LT, ST><<<nblocks, (sg.nb + 31) / 32 * 32, smem, st>>>(g, sg, U, res, x, m0 + (R)4,
+                                                                                 colour, mr_iters);
             count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             x_zero = false;

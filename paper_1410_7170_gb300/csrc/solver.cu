@@ -25,6 +25,7 @@ namespace ovl {
     do {                                                                           \
         cudaError_t e_ = (expr);                                                   \
         if (e_ != cudaSuccess) {                                                   \
+            cudaGetLastError();                                                    \
             c->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #expr; \
             return OVL_ECUDA;                                                      \
         }                                                                          \

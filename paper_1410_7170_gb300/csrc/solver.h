@@ -72,7 +72,7 @@ struct Ctx {
     GraphSlot graphs[4];
     // instrumentation
     bool prof = false;
-    ProfAcc pacc;
+    ProfAcc pacc[2];   // per precision slot (0 FP64, 1 FP32)
     long launch_mark = 0;
     cudaEvent_t ev[2][kMaxChunk * 4] = {};
     bool ev_ready[2] = {false, false};
