@@ -195,6 +195,26 @@ ovl_status ovl_prof_enable(ovl_ctx *ctx, int on);
 /* Reads the accumulated counters; reset = 1 zeroes them afterwards. */
 ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset);
 
+/* out = D_W(m0) in, the Wilson-Dirac operator of Eq. (Wilson-Dirac), for callers that cannot
+ * allocate device memory. The paper has no counterpart to this entry point; it exists for
+ * runtimes that own all device memory through their own pool, and for service loops that
+ * must not call cudaMalloc/cudaFree (cudaFree synchronises the whole device). It needs no
+ * context (ovl_create allocates) and calls no allocating routine.
+ * out, in: V*12 complex doubles, gauge: V*4*9 complex doubles, all DEVICE memory in the
+ * boundary layout above; dims as for ovl_create; antiperiodic: 1 = antiperiodic time boundary.
+ * The links are taken as SU(3) without a check (row 2 is rebuilt from rows 0 and 1).
+ * Working memory: one fixed device array inside the library of 16384 lattice sites
+ * (about 12.6 MB), reserved on every GPU that loads the library until the process exits;
+ * larger lattices are rejected with OVL_EINVAL. The first call on a device looks the
+ * array's address up on that device (make this first call before any stream capture).
+ * All calls share the array: calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and give undefined results; calls ordered on one stream are safe.
+ * The work is enqueued on cuda_stream (NULL = the legacy default stream) and the call
+ * returns without waiting: out is ready once that stream has finished it. Errors are
+ * reported by the return status, with the reason in ovl_last_error(NULL). */
+ovl_status wilson_apply_noalloc(double *out, const double *in, const double *gauge, const int dims[4],
+                                double m0, int antiperiodic, void *cuda_stream);
+
 /* Destroys the context and frees its device memory. NULL is a no-op. */
 ovl_status ovl_destroy(ovl_ctx *ctx);
 

@@ -74,7 +74,7 @@ class ovl_prof(ctypes.Structure):
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
-           "wilson_solve", "ovl_tuning"]
+           "wilson_solve", "ovl_tuning", "wilson_apply_noalloc"]
 
 _lib = None
 
@@ -102,6 +102,7 @@ def lib():
         L.ovl_prof_get.argtypes = [P, ctypes.POINTER(ovl_prof), I_]
         L.wilson_solve.argtypes = [P, P, P, D, D, ctypes.POINTER(I_)]
         L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
+        L.wilson_apply_noalloc.argtypes = [P, P, P, P, D, I_, P]
         for name in EXPORTS:
             if name not in ("ovl_last_error",):
                 getattr(L, name).restype = I_
@@ -190,6 +191,17 @@ def ovl_solve(ctx, x, b, n_rhs=1, tol=0.0, check=True):
     if check and st != OVL_OK:
         _check(st, ctx)
     return st, s.as_dict()
+
+
+def wilson_apply_noalloc(out, inp, gauge, dims, m0, antiperiodic=True, stream=None):
+    """out = D_W(m0) inp without a context and without device allocation (device tensors only).
+
+    Returns once the work is enqueued on `stream` (default: the legacy default stream)."""
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    _check(lib().wilson_apply_noalloc(_ptr(out, True), _ptr(inp), _ptr(gauge), ctypes.cast(d, ctypes.c_void_p),
+                                      float(m0), int(bool(antiperiodic)),
+                                      ctypes.c_void_p(stream) if stream else None), None)
+    return out
 
 
 def wilson_solve(ctx, x, b, m0, tol):

@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libovl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["dslash.cu", "blas.cu", "multishift.cu", "solver.cu", "api.cu", "sap.cu", "multirhs.cu"]
+CU_SOURCES = ["dslash.cu", "blas.cu", "multishift.cu", "solver.cu", "api.cu", "sap.cu", "multirhs.cu",
+              "noalloc.cu"]
 CXX_SOURCES = ["zolotarev.cpp"]
 
 

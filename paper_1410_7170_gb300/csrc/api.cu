@@ -25,6 +25,8 @@ using namespace ovl;
 
 static thread_local std::string g_create_error;
 
+void ovl::set_thread_error(const std::string &msg) { g_create_error = msg; }
+
 // ------------------------------------------------------------------ defaults
 extern "C" ovl_status ovl_params_default(ovl_params *p) {
     if (!p) return OVL_EINVAL;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace ovl {
@@ -128,6 +130,9 @@ cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, Ms
 void count_launches(long n);
 long launches_total();
 void set_launch_counting(bool on);
+
+// Message returned by ovl_last_error(NULL) on the calling thread.
+void set_thread_error(const std::string &msg);
 
 // ---------------------------------------------------------------- host Zolotarev
 int zolotarev_host(double k, int n, double *d0, double *a, double *c, double *delta);
