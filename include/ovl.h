@@ -190,6 +190,12 @@ typedef struct {
     int valid;              /* 1 if every event timing could be read */
 } ovl_prof;
 
+/* Times reps back-to-back full-lattice Wilson stencil launches (out = D_W(m0_ker) in on
+ * internal buffers, after 3 untimed launches) with CUDA events on the context's stream;
+ * precision 0 = FP64, 1 = FP32. *ms = average milliseconds per launch. Algorithmic traffic
+ * of one launch: 96 reals per site (4 links x 12, the input and the output spinor). */
+ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms);
+
 /* on = 1 enables event timing (allocates a small history buffer), 0 disables it. */
 ovl_status ovl_prof_enable(ovl_ctx *ctx, int on);
 /* Reads the accumulated counters; reset = 1 zeroes them afterwards. */
@@ -204,7 +210,7 @@ ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset);
  * boundary layout above; dims as for ovl_create; antiperiodic: 1 = antiperiodic time boundary.
  * The links are taken as SU(3) without a check (row 2 is rebuilt from rows 0 and 1).
  * Working memory: one fixed device array inside the library of 16384 lattice sites
- * (about 12.6 MB), reserved on every GPU that loads the library until the process exits;
+ * (about 15.7 MB), reserved on every GPU that loads the library until the process exits;
  * larger lattices are rejected with OVL_EINVAL. The first call on a device looks the
  * array's address up on that device (make this first call before any stream capture).
  * All calls share the array: calls whose work overlaps on the GPU (other streams, other

@@ -74,7 +74,7 @@ class ovl_prof(ctypes.Structure):
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
-           "wilson_solve", "ovl_tuning", "wilson_apply_noalloc"]
+           "wilson_solve", "ovl_tuning", "wilson_apply_noalloc", "ovl_dslash_time"]
 
 _lib = None
 
@@ -103,6 +103,7 @@ def lib():
         L.wilson_solve.argtypes = [P, P, P, D, D, ctypes.POINTER(I_)]
         L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
         L.wilson_apply_noalloc.argtypes = [P, P, P, P, D, I_, P]
+        L.ovl_dslash_time.argtypes = [P, I_, I_, ctypes.POINTER(D)]
         for name in EXPORTS:
             if name not in ("ovl_last_error",):
                 getattr(L, name).restype = I_
@@ -219,6 +220,13 @@ def ovl_tuning(ctx):
     return {"tps64": a.value, "tps32": b.value, "ms": ms.tolist()}
 
 
+def ovl_dslash_time(ctx, precision, reps=20):
+    """Average ms of one full-lattice Wilson stencil launch (precision 0 = FP64, 1 = FP32)."""
+    ms = ctypes.c_double()
+    _check(lib().ovl_dslash_time(ctx, int(precision), int(reps), ctypes.byref(ms)), ctx)
+    return ms.value
+
+
 def ovl_info(ctx):
     vals = [ctypes.c_double() for _ in range(7)]
     _check(lib().ovl_info(ctx, *[ctypes.byref(v) for v in vals]), ctx)
@@ -275,6 +283,9 @@ class Overlap:
 
     def tuning(self):
         return ovl_tuning(self.ctx)
+
+    def dslash_time(self, precision, reps=20):
+        return ovl_dslash_time(self.ctx, precision, reps)
 
     def prof_enable(self, on=True):
         ovl_prof_enable(self.ctx, on)

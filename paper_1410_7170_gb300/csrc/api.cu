@@ -273,7 +273,7 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, Iter iter_fn, int *iters_out
                 gs.prof = prof;
             }
             CK(cudaGraphLaunch(gs.exec, stream));
-            count_launches(4L * chunk);
+            count_launches(3L * chunk);
         } else {
             for (int k = 0; k < chunk; k++) CK(iter_fn(prof ? &ev[which][4 * k] : nullptr, 0u));
         }
@@ -623,6 +623,16 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
     c->g.Vh = (int)(V / 2);
     c->g.Lh3 = dims[3] / 2;
     c->g.antiperiodic = c->p.antiperiodic;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess) {
+            cudaGetLastError();
+            c->err = "no usable CUDA device";
+            return OVL_ECUDA;
+        }
+        c->g.nsm = nsm;
+    }
     c->n64 = V * 24;
     c->m0_ker = -rho_in;
     c->rho_in = rho_in;
@@ -662,7 +672,7 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
     ST(c->alloc(&buf, (size_t)2 * 128 * sizeof(double)));
     c->d_coef = (double *)buf;
     // gauge field
-    ST(c->alloc((void **)&c->U64, (size_t)V * 4 * 6 * sizeof(double2)));
+    ST(c->alloc((void **)&c->U64, (size_t)V * 4 * kLink64Words * sizeof(double2)));
     ST(c->alloc((void **)&c->U32, (size_t)V * 4 * 3 * sizeof(float4)));
     ST(c->alloc((void **)&c->io_lex, (size_t)c->n64 * sizeof(double)));
     ST(c->alloc((void **)&c->io_a, (size_t)c->n64 * sizeof(double)));
@@ -883,4 +893,42 @@ extern "C" ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, dou
     ST(wilson_solve_eo(c, c->io_a, c->io_b, m0, tol, &it));
     if (iters) *iters = it;
     return c->export_vec(c->io_b, x);
+}
+
+extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !ms || reps < 1 || (precision != 0 && precision != 1)) return OVL_EINVAL;
+    void *buf;
+    ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2));
+    CK(cudaMemsetAsync(buf, 0, (size_t)c->n64 * sizeof(double) * 2, c->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    ovl_status st = OVL_OK;
+    for (int k = 0; k < 3 + reps && st == OVL_OK; k++) {
+        if (k == 3 && cudaEventRecord(e0, c->stream) != cudaSuccess) st = OVL_ECUDA;
+        cudaError_t e;
+        if (precision == 0)
+            e = wilson_f64(c->g, c->U64, (const double2 *)buf, (double2 *)buf + (size_t)c->g.V * 12, c->m0_ker, 0, 1.0,
+                           nullptr, 0.0, c->stream);
+        else
+            e = wilson_f32(c->g, c->U32, (const float4 *)buf, (float4 *)buf + (size_t)c->g.V * 6, (float)c->m0_ker, 0,
+                           1.f, nullptr, 0.f, c->stream);
+        if (e != cudaSuccess) st = OVL_ECUDA;
+    }
+    float t = 0.f;
+    if (st == OVL_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        st = OVL_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), buf));
+    if (st != OVL_OK) {
+        cudaGetLastError();
+        c->err = "ovl_dslash_time: CUDA error";
+        return st;
+    }
+    *ms = t / reps;
+    return OVL_OK;
 }

@@ -8,9 +8,11 @@
 //   FP64 spinor: double2 [p][12 spin-colour][Vh]         (192 B per site)
 //   FP32 spinor: float4  [p][6 pairs of spin-colour][Vh] ( 96 B per site)
 //   FP16 spinor: uint4 (8 halves) [p][3][Vh] + float norm [p][Vh] (48+4 B per site)
-//   FP64 link:   double2 [p][mu][6][Vh]   rows 0 and 1 of U_mu(x) (12 reals)
-//   FP32 link:   float4  [p][mu][3][Vh]
-// Row 2 of an SU(3) link is rebuilt in registers as conj(row0 x row1).
+//   FP64 link:   double2 [p][mu][9][Vh]   all 18 reals of U_mu(x)
+//   FP32 link:   float4  [p][mu][3][Vh]   rows 0 and 1 (12 reals)
+// The FP32 stencils rebuild row 2 of an SU(3) link in registers as conj(row0 x row1);
+// the FP64 stencils, bound by the FP64 pipes rather than by memory, load all 18 reals
+// instead (the rebuild would cost about a fifth of their FP64 instructions).
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
@@ -60,7 +62,17 @@ struct Geom {
     int V;
     int antiperiodic;
     int tps64, tps32;   // threads per site of the FP64 / FP32 stencils (1 or 4), chosen by the autotuner
+    int nsm;            // streaming multiprocessors of the device (grid sizing)
 };
+
+// Site visited by thread t of a full-lattice kernel: parities interleave (t even: even
+// site, t odd: odd site, same checkerboard index), so the two sites that read a link
+// (x and x + mu) and the neighbours of a site are touched close together in time and
+// their data is still in L2.
+__device__ __forceinline__ void site_of_thread(int t, int &p, int &i) {
+    p = t & 1;
+    i = t >> 1;
+}
 
 // Coordinates of checkerboard site (p, i).
 __device__ __forceinline__ void eo_coords(const Geom &g, int p, int i, int x[4]) {
@@ -179,15 +191,15 @@ __device__ __forceinline__ void reconstruct_row2(cpx<R> u[3][3]) {
     u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
     u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
 }
+constexpr int kLink64Words = 9;   // double2 words per FP64 link
 template <typename R>
 __device__ __forceinline__ void load_link(const double2 *__restrict__ g, int Vh, int p, int mu, int i, cpx<R> u[3][3]) {
-    const double2 *b = g + ((size_t)(p * 4 + mu) * 6) * Vh + i;
+    const double2 *b = g + ((size_t)(p * 4 + mu) * kLink64Words) * Vh + i;
 #pragma unroll
-    for (int c = 0; c < 6; c++) {
+    for (int c = 0; c < 9; c++) {
         double2 v = __ldg(b + (size_t)c * Vh);
         u[c / 3][c % 3] = cpx<R>{(R)v.x, (R)v.y};
     }
-    reconstruct_row2(u);
 }
 template <typename R>
 __device__ __forceinline__ void load_link(const float4 *__restrict__ g, int Vh, int p, int mu, int i, cpx<R> u[3][3]) {

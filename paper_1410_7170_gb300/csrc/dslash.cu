@@ -53,9 +53,9 @@ __global__ void k_pack_gauge(Geom g, const double2 *__restrict__ lex, double2 *u
     x[2] = r % g.L[2]; r /= g.L[2];
     x[1] = r % g.L[1]; x[0] = r / g.L[1];
     const int p = (x[0] + x[1] + x[2] + x[3]) & 1, i = s >> 1;
-    double2 *d64 = u64 + ((size_t)(p * 4 + mu) * 6) * g.Vh + i;
+    double2 *d64 = u64 + ((size_t)(p * 4 + mu) * kLink64Words) * g.Vh + i;
 #pragma unroll
-    for (int c = 0; c < 6; c++) d64[(size_t)c * g.Vh] = make_double2(u[c / 3][c % 3].re, u[c / 3][c % 3].im);
+    for (int c = 0; c < 9; c++) d64[(size_t)c * g.Vh] = make_double2(u[c / 3][c % 3].re, u[c / 3][c % 3].im);
     float4 *d32 = u32 + ((size_t)(p * 4 + mu) * 3) * g.Vh + i;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -150,12 +150,13 @@ cudaError_t spinor_f2d(const Geom &g, const float4 *a, double2 *b, cudaStream_t 
 // out = a [g5] D_W(m0) in + b z, one thread per site of the full lattice
 // (threads [0, Vh) even sites, [Vh, V) odd sites).
 template <typename R, typename LT, typename ST>
-__global__ void __launch_bounds__(kBlock) k_wilson(Geom g, const LT *__restrict__ U, const ST *__restrict__ in,
+__global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_wilson(Geom g, const LT *__restrict__ U, const ST *__restrict__ in,
                                                    ST *__restrict__ out, R m4, int g5, R a,
                                                    const ST *z, R b) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.V) return;
-    const int p = t >= g.Vh, i = t - p * g.Vh;
+    int p, i;
+    site_of_thread(t, p, i);
     cpx<R> hop[12], own[12], res[12];
     wilson_hop<R>(g, U, in, p, i, hop);
     load_spinor<R>(in, g.Vh, p, i, own);
@@ -176,12 +177,13 @@ __global__ void __launch_bounds__(kBlock) k_wilson(Geom g, const LT *__restrict_
 // Same with four threads per site (thread q of a quad owns direction mu = q and the
 // storage words j with j % 4 == q of the output).
 template <typename R, typename LT, typename ST>
-__global__ void __launch_bounds__(kBlock) k_wilson4(Geom g, const LT *__restrict__ U, const ST *__restrict__ in,
+__global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_wilson4(Geom g, const LT *__restrict__ U, const ST *__restrict__ in,
                                                     ST *__restrict__ out, R m4, int g5, R a, const ST *z, R b) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int s0 = t >> 2, q = t & 3;
     const int s = s0 < g.V ? s0 : g.V - 1;   // quads past the end compute a copy, store nothing
-    const int p = s >= g.Vh, i = s - p * g.Vh;
+    int p, i;
+    site_of_thread(s, p, i);
     cpx<R> acc[12];
     wilson_hop_dir<R>(g, U, in, p, i, q, acc);
     quad_allreduce(acc);
@@ -214,8 +216,10 @@ cudaError_t wilson_f64(const Geom &g, const double2 *U, const double2 *in, doubl
     if (g.tps64 == 4)
         k_wilson4<double, double2, double2><<<plain_grid(4L * g.V), kBlock, 0, st>>>(g, U, in, out, m0 + 4.0, g5,
                                                                                      a, z, b);
-    else
-        k_wilson<double, double2, double2><<<plain_grid(g.V), kBlock, 0, st>>>(g, U, in, out, m0 + 4.0, g5, a, z, b);
+    else {
+        const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<double>::value, 1 << 30);
+        k_wilson<double, double2, double2><<<ls.grid, ls.block, 0, st>>>(g, U, in, out, m0 + 4.0, g5, a, z, b);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -224,8 +228,10 @@ cudaError_t wilson_f32(const Geom &g, const float4 *U, const float4 *in, float4 
     if (g.tps32 == 4)
         k_wilson4<float, float4, float4><<<plain_grid(4L * g.V), kBlock, 0, st>>>(g, U, in, out, m0 + 4.0f, g5, a,
                                                                                   z, b);
-    else
-        k_wilson<float, float4, float4><<<plain_grid(g.V), kBlock, 0, st>>>(g, U, in, out, m0 + 4.0f, g5, a, z, b);
+    else {
+        const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<float>::value, 1 << 30);
+        k_wilson<float, float4, float4><<<ls.grid, ls.block, 0, st>>>(g, U, in, out, m0 + 4.0f, g5, a, z, b);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -21,12 +21,42 @@ struct RedScratch {
     unsigned *counter;     // one word, zero between launches
 };
 
+// Minimum resident blocks per SM requested from the compiler: the FP64 stencils are
+// held to 128 registers so two 256-thread blocks fit on an SM (one wave of 256 blocks
+// at 16^4 on 152 SMs).
+template <typename R> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<double> { static constexpr int value = 2; };
+template <> struct MinBlocks<float> { static constexpr int value = 2; };
+
 inline int red_grid(long n_threads) {
     long b = (n_threads + kBlock - 1) / kBlock;
     if (b > kMaxRedBlocks) b = kMaxRedBlocks;
     if (b < 1) b = 1;
     return (int)b;
 }
+// Grid for n_threads site-threads: the block count is a multiple of nsm * per_sm (every
+// SM gets the same number of resident blocks in every wave), the block size a multiple of
+// 32 up to kBlock, and at most max_blocks blocks (beyond that the kernel strides).
+struct LaunchShape {
+    int grid, block;
+};
+inline LaunchShape balanced_shape(long n_threads, int nsm, int per_sm, int max_blocks) {
+    if (nsm <= 0) nsm = 1;
+    const long slots = (long)nsm * per_sm;
+    long waves = (n_threads + slots * kBlock - 1) / (slots * kBlock);
+    if (waves < 1) waves = 1;
+    long nblk = slots * waves;
+    if (nblk > max_blocks) nblk = (max_blocks / slots) * slots;
+    if (nblk < 1) nblk = 1;
+    long per_block = (n_threads + nblk - 1) / nblk;
+    int T = (int)((per_block + 31) / 32 * 32);
+    if (T > kBlock) T = kBlock;
+    if (T < 32) T = 32;
+    long used = (n_threads + T - 1) / T;   // drop blocks that would get no site
+    if (used < nblk) nblk = used;
+    return LaunchShape{(int)nblk, T};
+}
+
 inline int plain_grid(long n_threads) {
     long b = (n_threads + kBlock - 1) / kBlock;
     return (int)(b < 1 ? 1 : b);

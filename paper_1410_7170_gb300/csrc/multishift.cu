@@ -46,24 +46,29 @@ struct AlphaFin {
     }
 };
 
+// Shift scalars after the residual update, one warp: lane j handles shifts j, j+32.
 struct ShiftFin {
     MsState *s;
-    __device__ void operator()(const double *v) const {
+    __device__ void operator()(const double *v, int lane) const {
         const double rr_new = v[0];
-        const double a = s->alpha, ap = s->alpha_prev, bp = s->beta_prev;
-        const double beta = rr_new / s->rr;
+        const double a = s->alpha, ap = s->alpha_prev, bp = s->beta_prev, rr_old = s->rr;
+        const double beta = rr_new / rr_old;
+        const int n = s->n;
         if (!isfinite(beta)) {
-            s->status = 1;
-            s->done = 1;
+            if (lane == 0) {
+                s->status = 1;
+                s->done = 1;
+            }
             return;
         }
-        const double rnorm = sqrt(rr_new), bnorm = sqrt(s->bb);
-        int any = 0;
-        for (int l = 0; l < s->n; l++) {
+        const double rnorm = sqrt(rr_new), bnorm = sqrt(s->bb), tolb = s->tol * bnorm;
+        int any = 0, nupd = 0;
+        for (int l = lane; l < n; l += 32) {
             if (!s->active[l]) {
                 s->alpha_l[l] = 0.0;
                 continue;
             }
+            nupd++;
             double zn;
             if (l == 0) {
                 zn = 1.0;
@@ -78,32 +83,35 @@ struct ShiftFin {
             s->zeta_prev[l] = s->zeta[l];
             s->zeta[l] = zn;
             // residual bound after this iteration's update: drop the shift next time
-            if (s->crit[l] * fabs(zn) * rnorm <= s->tol * bnorm) s->active[l] = 2;   // last update
+            if (s->crit[l] * fabs(zn) * rnorm <= tolb) s->active[l] = 2;   // last update
             else any = 1;
         }
-        // the base direction p_0 drives the Krylov space: keep it while any shift is live
-        if (any && s->active[0] == 2) s->active[0] = 1;
-        if (s->hist && s->iter < s->hist_cap) {
-            int nu = 0;
-            for (int l = 0; l < s->n; l++) nu += s->active[l] != 0;
-            s->hist[s->iter] = nu;
+        any = __any_sync(0xffffffffu, any);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nupd += __shfl_down_sync(0xffffffffu, nupd, off);
+        __syncwarp();
+        if (lane == 0) {
+            // the base direction p_0 drives the Krylov space: keep it while any shift is live
+            if (any && s->active[0] == 2) s->active[0] = 1;
+            if (s->hist && s->iter < s->hist_cap) s->hist[s->iter] = nupd;
+            s->alpha_prev = a;
+            s->beta_prev = beta;
+            s->rr = rr_new;
+            s->iter += 1;
+            if (!any) s->done = 2;   // finish this iteration's shift updates, then stop
         }
-        s->alpha_prev = a;
-        s->beta_prev = beta;
-        s->rr = rr_new;
-        s->iter += 1;
-        if (!any) s->done = 2;   // finish this iteration's shift updates, then stop
     }
 };
 
 // t = gamma5 D_W(m) p0 ; reduce ||t||^2, ||p0||^2
 template <typename R, typename LT, typename ST>
-__global__ void __launch_bounds__(kBlock) k_ms_q(Geom g, const LT *__restrict__ U, R m4, MsState *s,
+__global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, const LT *__restrict__ U, R m4, MsState *s,
                                                  const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs) {
     if (s->done) return;
     double v[2] = {0.0, 0.0};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
-        const int p = k >= g.Vh, i = k - p * g.Vh;
+        int p, i;
+        site_of_thread(k, p, i);
         cpx<R> hop[12], own[12], res[12];
         wilson_hop<R>(g, U, p0, p, i, hop);
         load_spinor<R>(p0, g.Vh, p, i, own);
@@ -124,14 +132,15 @@ __global__ void __launch_bounds__(kBlock) k_ms_q(Geom g, const LT *__restrict__ 
 
 // r -= alpha (gamma5 D_W(m) t + sigma0 p0) ; reduce ||r||^2 ; shift scalars
 template <typename R, typename LT, typename ST>
-__global__ void __launch_bounds__(kBlock) k_ms_r(Geom g, const LT *__restrict__ U, R m4, MsState *s,
+__global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r(Geom g, const LT *__restrict__ U, R m4, MsState *s,
                                                  const ST *__restrict__ t, const ST *__restrict__ p0,
                                                  ST *__restrict__ r, RedScratch rs) {
     if (s->done) return;
     const R alpha = (R)s->alpha, sig0 = (R)s->sigma[0];
     double v[1] = {0.0};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
-        const int p = k >= g.Vh, i = k - p * g.Vh;
+        int p, i;
+        site_of_thread(k, p, i);
         cpx<R> hop[12], own[12], res[12], pp[12], rv[12];
         wilson_hop<R>(g, U, t, p, i, hop);
         load_spinor<R>(t, g.Vh, p, i, own);
@@ -148,13 +157,13 @@ __global__ void __launch_bounds__(kBlock) k_ms_r(Geom g, const LT *__restrict__ 
         v[0] += (double)a0;
         store_spinor<R>(r, g.Vh, p, i, rv);
     }
-    grid_reduce<1>(v, rs, ShiftFin{s});
+    grid_reduce_warp<1>(v, rs, ShiftFin{s});
 }
 
 // Four-threads-per-site versions (see wilson_quad.cuh). The loops stride by whole
 // blocks so every lane of a warp runs the same trip count (the shuffles need all lanes).
 template <typename R, typename LT, typename ST>
-__global__ void __launch_bounds__(kBlock) k_ms_q4(Geom g, const LT *__restrict__ U, R m4, MsState *s,
+__global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q4(Geom g, const LT *__restrict__ U, R m4, MsState *s,
                                                   const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs) {
     if (s->done) return;
     using C = Chunk<ST>;
@@ -164,7 +173,8 @@ __global__ void __launch_bounds__(kBlock) k_ms_q4(Geom g, const LT *__restrict__
         const long tt = base + threadIdx.x;
         const int s0 = (int)(tt >> 2), q = (int)(tt & 3);
         const int site = s0 < g.V ? s0 : g.V - 1;
-        const int p = site >= g.Vh, i = site - p * g.Vh;
+        int p, i;
+        site_of_thread(site, p, i);
         cpx<R> acc[12];
         wilson_hop_dir<R>(g, U, p0, p, i, q, acc);
         quad_allreduce(acc);
@@ -192,7 +202,7 @@ __global__ void __launch_bounds__(kBlock) k_ms_q4(Geom g, const LT *__restrict__
 }
 
 template <typename R, typename LT, typename ST>
-__global__ void __launch_bounds__(kBlock) k_ms_r4(Geom g, const LT *__restrict__ U, R m4, MsState *s,
+__global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r4(Geom g, const LT *__restrict__ U, R m4, MsState *s,
                                                   const ST *__restrict__ t, const ST *__restrict__ p0,
                                                   ST *__restrict__ r, RedScratch rs) {
     if (s->done) return;
@@ -204,7 +214,8 @@ __global__ void __launch_bounds__(kBlock) k_ms_r4(Geom g, const LT *__restrict__
         const long tt = base + threadIdx.x;
         const int s0 = (int)(tt >> 2), q = (int)(tt & 3);
         const int site = s0 < g.V ? s0 : g.V - 1;
-        const int p = site >= g.Vh, i = site - p * g.Vh;
+        int p, i;
+        site_of_thread(site, p, i);
         cpx<R> acc[12];
         wilson_hop_dir<R>(g, U, t, p, i, q, acc);
         quad_allreduce(acc);
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(kBlock) k_ms_r4(Geom g, const LT *__restrict__
             C::template store<R>(r, g.Vh, p, i, j, rv);
         }
     }
-    grid_reduce<1>(v, rs, ShiftFin{s});
+    grid_reduce_warp<1>(v, rs, ShiftFin{s});
 }
 
 // Elementwise access to a storage word as NR reals.
@@ -254,7 +265,7 @@ template <> struct Word<float4> {
 // four independent memory requests in flight.
 template <typename ST>
 __global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__restrict__ r, ST *__restrict__ y,
-                                                      ST *__restrict__ P, long stride, long nw) {
+                                                      ST *__restrict__ P, long stride, long nw, unsigned *counter) {
     using A = typename Word<ST>::A;
     __shared__ A sw[kMaxPoles], sz[kMaxPoles], sb[kMaxPoles];
     __shared__ int sidx[kMaxPoles];
@@ -302,14 +313,13 @@ __global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__re
         }
         y[k] = Word<ST>::put(yv);
     }
-}
-
-// Retire shifts marked for a last update, and finish when none is left.
-__global__ void k_ms_retire(MsState *s) {
-    if (s->done == 1) return;
-    for (int l = 0; l < s->n; l++)
-        if (s->active[l] == 2) s->active[l] = 0;
-    if (s->done == 2) s->done = 1;
+    // the last block retires the shifts that made their final update and ends a finished solve
+    if (grid_last_block(counter)) {
+        for (int l = threadIdx.x; l < s->n; l += blockDim.x)
+            if (s->active[l] == 2) s->active[l] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0 && s->done == 2) s->done = 1;
+    }
 }
 
 struct InitFin {
@@ -356,19 +366,19 @@ template <typename R, typename LT, typename ST>
 cudaError_t ms_iter_t(const Geom &g, const LT *U, R m0, MsState *s, MsVectors<ST> v, RedScratch rs,
                       cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
     const int tps = sizeof(R) == 8 ? g.tps64 : g.tps32;
-    const int gs = red_grid(tps == 4 ? 4L * g.V : (long)g.V);
+    const int gs = red_grid(4L * g.V);
+    const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<R>::value, kMaxRedBlocks);
     cudaError_t e;
     if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
     if (tps == 4) k_ms_q4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
-    else k_ms_q<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
+    else k_ms_q<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
     if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
     if (tps == 4) k_ms_r4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
-    else k_ms_r<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
+    else k_ms_r<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
     if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
-    k_ms_shifts<ST><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.y, v.p, v.stride, v.stride);
+    k_ms_shifts<ST><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.y, v.p, v.stride, v.stride, rs.counter);
     if (ev && (e = cudaEventRecordWithFlags(ev[3], st, ev_flags)) != cudaSuccess) return e;
-    k_ms_retire<<<1, 1, 0, st>>>(s);
-    count_launches(4);
+    count_launches(3);
     return cudaGetLastError();
 }
 

@@ -9,9 +9,9 @@
 // its working memory is one file-scope device array of fixed size, reserved when the
 // library is loaded and held by every GPU that loads it until the process exits.
 //
-// Working memory (FP64, even-odd layouts of the library): 12-real links of all four
+// Working memory (FP64, even-odd layouts of the library): the links of all four
 // directions, the packed input spinor and the packed output spinor, for at most
-// kNoAllocMaxSites lattice sites (about 12.6 MB in total).
+// kNoAllocMaxSites lattice sites (about 15.7 MB in total).
 #include <mutex>
 #include <string>
 
@@ -21,7 +21,7 @@
 namespace ovl {
 
 constexpr long kNoAllocMaxSites = 16384;
-constexpr size_t kNoAllocLinkBytes = (size_t)kNoAllocMaxSites * 4 * 6 * sizeof(double2);
+constexpr size_t kNoAllocLinkBytes = (size_t)kNoAllocMaxSites * 4 * kLink64Words * sizeof(double2);
 constexpr size_t kNoAllocSpinorBytes = (size_t)kNoAllocMaxSites * 12 * sizeof(double2);
 constexpr size_t kNoAllocBytes = kNoAllocLinkBytes + 2 * kNoAllocSpinorBytes;
 
@@ -31,8 +31,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 
-// Rows 0 and 1 of every link into the FP64 12-real even-odd layout (no SU(3) check:
-// the caller's links are taken as SU(3); row 2 is rebuilt from rows 0 and 1).
+// Every link into the FP64 even-odd link layout of the library (all 18 reals).
 __global__ void k_noalloc_pack_links(Geom g, const double2 *__restrict__ lex) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)g.V * 4) return;
@@ -44,9 +43,9 @@ __global__ void k_noalloc_pack_links(Geom g, const double2 *__restrict__ lex) {
     const int x0 = r / g.L[1];
     const int p = (x0 + x1 + x2 + x3) & 1, i = s >> 1;
     double2 *links = reinterpret_cast<double2 *>(g_noalloc_scratch);
-    double2 *d = links + ((size_t)(p * 4 + mu) * 6) * g.Vh + i;
+    double2 *d = links + ((size_t)(p * 4 + mu) * kLink64Words) * g.Vh + i;
 #pragma unroll
-    for (int c = 0; c < 6; c++) d[(size_t)c * g.Vh] = lex[(size_t)t * 9 + (c / 3) * 3 + c % 3];
+    for (int c = 0; c < 9; c++) d[(size_t)c * g.Vh] = lex[(size_t)t * 9 + c];
 }
 
 std::mutex g_noalloc_mu;
@@ -118,6 +117,10 @@ extern "C" ovl_status wilson_apply_noalloc(double *out, const double *in, const 
     g.Lh3 = dims[3] / 2;
     g.antiperiodic = antiperiodic ? 1 : 0;
     g.tps64 = g.tps32 = 1;
+    if (cudaDeviceGetAttribute(&g.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(OVL_ECUDA, "wilson_apply_noalloc: cannot query the device");
+    }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     double2 *links = (double2 *)scratch;
     double2 *pin = (double2 *)(scratch + kNoAllocLinkBytes);

@@ -66,4 +66,60 @@ __device__ __forceinline__ void grid_reduce(double v[NV], RedScratch rs, Fin fin
     }
 }
 
+// As grid_reduce, but the last block runs fin(total, lane) on all 32 lanes of its first
+// warp (for finalisations that are parallel over a small index, e.g. one lane per shift).
+template <int NV, typename Fin>
+__device__ __forceinline__ void grid_reduce_warp(double v[NV], RedScratch rs, Fin fin) {
+    __shared__ int is_last;
+    __shared__ double tot[NV];
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) rs.partials[k * kMaxRedBlocks + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned t = atomicAdd(rs.counter, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            s[k] = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+                s[k] += __ldcg(rs.partials + k * kMaxRedBlocks + b);
+        }
+        block_sum<NV>(s);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NV; k++) tot[k] = s[k];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double t2[NV];
+#pragma unroll
+            for (int k = 0; k < NV; k++) t2[k] = tot[k];
+            fin(t2, (int)threadIdx.x);
+            if (threadIdx.x == 0) *rs.counter = 0u;
+        }
+    }
+}
+
+// Last-block detection without values: returns true in every thread of the block that
+// finishes last (after a fence that makes all blocks' global writes visible to it) and
+// resets the counter. Must be reached by every thread of every block.
+__device__ __forceinline__ bool grid_last_block(unsigned *counter) {
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1);
+        if (is_last) *counter = 0u;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
 }  // namespace ovl

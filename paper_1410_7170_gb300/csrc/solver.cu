@@ -145,6 +145,7 @@ static ovl_status fgmres(Ctx *c, Krylov<T> &k, T *x, const T *b, double tol, int
         return OVL_OK;
     }
     bool xz = x_zero;
+    if (xz) CK(cudaMemsetAsync(x, 0, n * sizeof(T), c->stream));   // x_zero: start from x = 0
     std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m), h1(m + 1), h2(m + 1);
     while (true) {
         // r = b - A x

@@ -1,0 +1,57 @@
+"""Runs one operation of a workload through the library's public API, for external
+profilers (ncu). Nothing is timed here; the benchmark is bench.py.
+
+    python -m paper_1410_7170_gb300.profile_run --what solve_mixed|solve_fp64|sign64|dslash64|dslash32
+        [--lattice 16x16x16x16] [--stout 3]
+
+The gauge field, right-hand side and solver settings are those of bench.py's 16^4
+workload (seeded links exp(i 0.5 H) smeared by 3 stout steps, rho = 1, mu = 0.01,
+one Gaussian right-hand side, tol 1e-8).
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    import torch
+
+    import paper_1410_7170_gb300 as ovl
+    import synth
+    from paper_1410_7170_gb300 import build
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--what", required=True,
+                    choices=["solve_mixed", "solve_fp64", "sign64", "dslash64", "dslash32"])
+    ap.add_argument("--lattice", default="16x16x16x16")
+    ap.add_argument("--stout", type=int, default=3)
+    a = ap.parse_args()
+    build.build()
+    dims = tuple(int(v) for v in a.lattice.split("x"))
+    U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1002, stout_steps=a.stout)).cuda()
+    b = torch.from_numpy(synth.rhs_gaussian(dims, 2002)).cuda()
+    if a.what == "solve_mixed":
+        p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32)
+    elif a.what == "solve_fp64":
+        p = ovl.params_default(precond=ovl.OVL_PREC_WILSON, precision=ovl.OVL_FP64, prec_max_iter=4)
+    else:
+        p = ovl.params_default()
+    op = ovl.Overlap(U, dims, 1.0, 0.01, p)
+    x = torch.zeros_like(b)
+    if a.what.startswith("solve"):
+        st, stats = op.ovl_solve(x, b, 1, 1e-8)
+        print(stats)
+    elif a.what == "sign64":
+        op.sign_apply(x, b, 1e-8)
+    else:
+        print(op.dslash_time(0 if a.what == "dslash64" else 1, 3), "ms")
+    torch.cuda.synchronize()
+    op.close()
+
+
+if __name__ == "__main__":
+    main()
