@@ -51,8 +51,8 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->max_ms_iter = 20000;
     for (int m = 0; m < 4; m++) p->sap_block[m] = 4;
     p->sap_cycles = 2;
-    p->sap_mr_iters = 4;
-    p->prec_restart = 16;
+    p->sap_mr_iters = 6;
+    p->prec_restart = 32;
     p->prec_max_iter = 64;
     p->rhs_block = 1;
     p->use_graphs = 1;
@@ -239,12 +239,12 @@ ovl_status Ctx::ms_setup(MsState *d_state, double tol) {
 // device logs how many shifts each iteration updated, so per-kernel durations and
 // algorithmic bytes come from the same launches that do the work.
 template <typename Iter>
-ovl_status Ctx::ms_run(MsState *d_state, int which, Iter iter_fn, int *iters_out) {
+ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes, Iter iter_fn, int *iters_out) {
     Ctx *c = this;
     const int chunk = std::min(p.check_every, kMaxChunk);
     const double rbytes = which == 0 ? 8.0 : 4.0;
     int done_iters = 0, iter_before = 0;
-    GraphSlot &gs = graphs[which];
+    GraphSlot &gs = graphs[slot];
     if (prof && !ev_ready[which]) {
         for (int k = 0; k < kMaxChunk * 4; k++) CK(cudaEventCreate(&ev[which][k]));
         ev_ready[which] = true;
@@ -302,7 +302,7 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, Iter iter_fn, int *iters_out
                 // shifts: r, y in/out, each updated p_l in/out
                 pa.q_bytes += 96.0 * V * rbytes;
                 pa.r_bytes += 144.0 * V * rbytes;
-                pa.s_bytes += (72.0 + 48.0 * h_hist[k]) * V * rbytes;
+                pa.s_bytes += (72.0 * rbytes + shift_bytes * h_hist[k]) * V;
             }
         }
         iter_before = iter;
@@ -332,7 +332,7 @@ ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
     CK(ms_init_f64(g, npole, ms64_state, ms64, b, rs, stream));
     int iters = 0;
     auto fn = [&](cudaEvent_t *e, unsigned f) { return ms_iter_f64(g, U64, m0_ker, ms64_state, ms64, rs, stream, e, f); };
-    ST(ms_run(ms64_state, 0, fn, &iters));
+    ST(ms_run(ms64_state, 0, 0, 48.0 * 8.0, fn, &iters));
     stat_ms64 += iters;
     const double sc = zd0 / lam_min;
     if (mode == 0) CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 1, sc, nullptr, 0.0, stream));
@@ -343,18 +343,32 @@ ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
 // FP32 version for the inner (low-accuracy) D_N: b, out FP32 eo spinors.
 ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
     Ctx *c = this;
-    ST(ensure_ms32());
-    ST(ms_setup(ms32_state, tol));
-    CK(ms_init_f32(g, npole, ms32_state, ms32, b, rs, stream));
     int iters = 0;
-    auto fn = [&](cudaEvent_t *e, unsigned f) {
-        return ms_iter_f32(g, U32, (float)m0_ker, ms32_state, ms32, rs, stream, e, f);
-    };
-    ST(ms_run(ms32_state, 1, fn, &iters));
+    const float4 *y;
+    if (p.precision == OVL_MIXED_HALF) {
+        // shifted directions stored in FP16 (per site: 48 B + 4 B norm read and written)
+        ST(ensure_msh());
+        ST(ms_setup(msh_state, tol));
+        CK(ms_init_half(g, npole, msh_state, msh, b, rs, stream));
+        auto fn = [&](cudaEvent_t *e, unsigned f) {
+            return ms_iter_half(g, U32, (float)m0_ker, msh_state, msh, rs, stream, e, f);
+        };
+        ST(ms_run(msh_state, 1, 2, 104.0, fn, &iters));
+        y = msh.y;
+    } else {
+        ST(ensure_ms32());
+        ST(ms_setup(ms32_state, tol));
+        CK(ms_init_f32(g, npole, ms32_state, ms32, b, rs, stream));
+        auto fn = [&](cudaEvent_t *e, unsigned f) {
+            return ms_iter_f32(g, U32, (float)m0_ker, ms32_state, ms32, rs, stream, e, f);
+        };
+        ST(ms_run(ms32_state, 1, 1, 48.0 * 4.0, fn, &iters));
+        y = ms32.y;
+    }
     stat_ms32 += iters;
     const float sc = (float)(zd0 / lam_min);
-    if (mode == 0) CK(wilson_f32(g, U32, ms32.y, out, (float)m0_ker, 1, sc, nullptr, 0.f, stream));
-    else CK(wilson_f32(g, U32, ms32.y, out, (float)m0_ker, 0, sc, b, (float)rho, stream));
+    if (mode == 0) CK(wilson_f32(g, U32, y, out, (float)m0_ker, 1, sc, nullptr, 0.f, stream));
+    else CK(wilson_f32(g, U32, y, out, (float)m0_ker, 0, sc, b, (float)rho, stream));
     return OVL_OK;
 }
 
@@ -371,6 +385,30 @@ ovl_status Ctx::ensure_ms64() {
     ms64.stride = words;
     return OVL_OK;
 }
+ovl_status Ctx::ensure_msh() {
+    if (msh.ph) return OVL_OK;
+    if (!msh_state) {
+        void *sb;
+        ST(alloc(&sb, sizeof(MsState)));
+        msh_state = (MsState *)sb;
+    }
+    const long words = (long)g.V * 6, words_h = (long)g.V * 3;
+    const int nh = npole > 1 ? npole - 1 : 1;
+    void *buf;
+    ST(alloc(&buf, (size_t)words * sizeof(float4) * 4 + (size_t)words_h * sizeof(uint4) * nh +
+                       (size_t)g.V * sizeof(float) * nh));
+    float4 *f = (float4 *)buf;
+    msh.r = f;
+    msh.t = f + words;
+    msh.y = f + 2 * words;
+    msh.p0 = f + 3 * words;
+    msh.ph = (uint4 *)(f + 4 * words);
+    msh.pn = (float *)(msh.ph + (size_t)words_h * nh);
+    msh.words = words;
+    msh.words_h = words_h;
+    return OVL_OK;
+}
+
 ovl_status Ctx::ensure_ms32() {
     if (ms32.p) return OVL_OK;
     const long words = (long)g.V * 6;    // float4 per vector

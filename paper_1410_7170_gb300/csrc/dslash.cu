@@ -16,6 +16,24 @@ void count_launches(long n) {
 long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 void set_launch_counting(bool on) { g_counting = on; }
 
+int device_sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 // ------------------------------------------------------------------ gauge upload
 // One thread per (site, mu): SU(3) check, then rows 0 and 1 into both precisions.
 __global__ void k_pack_gauge(Geom g, const double2 *__restrict__ lex, double2 *u64, float4 *u32, int *bad,
@@ -152,9 +170,9 @@ cudaError_t spinor_f2d(const Geom &g, const float4 *a, double2 *b, cudaStream_t 
 template <typename R, typename LT, typename ST>
 __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_wilson(Geom g, const LT *__restrict__ U, const ST *__restrict__ in,
                                                    ST *__restrict__ out, R m4, int g5, R a,
-                                                   const ST *z, R b) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g.V) return;
+                                                   const ST *z, R b, int spb) {
+    const int t = blockIdx.x * spb + threadIdx.x;
+    if (threadIdx.x >= spb || t >= g.V) return;
     int p, i;
     site_of_thread(t, p, i);
     cpx<R> hop[12], own[12], res[12];
@@ -218,7 +236,8 @@ cudaError_t wilson_f64(const Geom &g, const double2 *U, const double2 *in, doubl
                                                                                      a, z, b);
     else {
         const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<double>::value, 1 << 30);
-        k_wilson<double, double2, double2><<<ls.grid, ls.block, 0, st>>>(g, U, in, out, m0 + 4.0, g5, a, z, b);
+        k_wilson<double, double2, double2><<<ls.grid, ls.block, 0, st>>>(g, U, in, out, m0 + 4.0, g5, a, z, b,
+                                                                         ls.spb);
     }
     count_launches(1);
     return cudaGetLastError();
@@ -230,7 +249,8 @@ cudaError_t wilson_f32(const Geom &g, const float4 *U, const float4 *in, float4 
                                                                                   z, b);
     else {
         const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<float>::value, 1 << 30);
-        k_wilson<float, float4, float4><<<ls.grid, ls.block, 0, st>>>(g, U, in, out, m0 + 4.0f, g5, a, z, b);
+        k_wilson<float, float4, float4><<<ls.grid, ls.block, 0, st>>>(g, U, in, out, m0 + 4.0f, g5, a, z, b,
+                                                                      ls.spb);
     }
     count_launches(1);
     return cudaGetLastError();

@@ -28,33 +28,38 @@ template <typename R> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<double> { static constexpr int value = 2; };
 template <> struct MinBlocks<float> { static constexpr int value = 2; };
 
+// SMs of the current device (queried once per device and cached).
+int device_sm_count();
+
+// Blocks of a grid-striding reduction over n_threads elements: enough to fill every SM a
+// few times, few enough that the per-block partials and the arrival counter stay cheap.
 inline int red_grid(long n_threads) {
     long b = (n_threads + kBlock - 1) / kBlock;
+    const long cap = 4L * device_sm_count();
+    if (b > cap) b = cap;
     if (b > kMaxRedBlocks) b = kMaxRedBlocks;
     if (b < 1) b = 1;
     return (int)b;
 }
-// Grid for n_threads site-threads: the block count is a multiple of nsm * per_sm (every
-// SM gets the same number of resident blocks in every wave), the block size a multiple of
-// 32 up to kBlock, and at most max_blocks blocks (beyond that the kernel strides).
+// Launch shape for a site-parallel kernel over n sites: the block count is a multiple of
+// nsm * per_sm (every SM holds the same number of blocks in every wave), each block owns
+// spb consecutive sites (thread t < spb of block b handles site b * spb + t, striding by
+// grid * spb), and the block size is spb rounded up to whole warps.
 struct LaunchShape {
-    int grid, block;
+    int grid, block, spb;
 };
-inline LaunchShape balanced_shape(long n_threads, int nsm, int per_sm, int max_blocks) {
+inline LaunchShape balanced_shape(long n, int nsm, int per_sm, int max_blocks) {
     if (nsm <= 0) nsm = 1;
     const long slots = (long)nsm * per_sm;
-    long waves = (n_threads + slots * kBlock - 1) / (slots * kBlock);
+    long waves = (n + slots * kBlock - 1) / (slots * kBlock);
     if (waves < 1) waves = 1;
     long nblk = slots * waves;
     if (nblk > max_blocks) nblk = (max_blocks / slots) * slots;
     if (nblk < 1) nblk = 1;
-    long per_block = (n_threads + nblk - 1) / nblk;
-    int T = (int)((per_block + 31) / 32 * 32);
-    if (T > kBlock) T = kBlock;
-    if (T < 32) T = 32;
-    long used = (n_threads + T - 1) / T;   // drop blocks that would get no site
-    if (used < nblk) nblk = used;
-    return LaunchShape{(int)nblk, T};
+    long spb = (n + nblk - 1) / nblk;
+    if (spb > kBlock) spb = kBlock;   // more sites than threads: the kernel strides
+    const int T = (int)((spb + 31) / 32 * 32);
+    return LaunchShape{(int)nblk, T, (int)spb};
 }
 
 inline int plain_grid(long n_threads) {
@@ -144,7 +149,18 @@ struct MsVectors {
     long stride; // elements of ST per vector
 };
 
-// One multishift iteration = four launches (Q p, residual update, shift updates, retire).
+// Half-precision variant of the FP32 multishift vectors: p_0 (the base direction, which
+// drives the Krylov process), r, t and y stay FP32; the shifted directions p_l, l >= 1,
+// are stored as FP16 scaled by a per-site FP32 norm (see HalfSpinor).
+struct MsVectorsH {
+    float4 *r, *t, *y, *p0;
+    uint4 *ph;          // p_l for l >= 1 at ph + (l - 1) * words_h
+    float *pn;          // their per-site norms at pn + (l - 1) * V
+    long words;         // float4 words per FP32 vector (6 V)
+    long words_h;       // uint4 words per FP16 vector (3 V)
+};
+
+// One multishift iteration = three launches (Q p, residual update, shift updates).
 // ev (optional, 4 events): recorded before/between/after the first three launches;
 // ev_flags is passed to cudaEventRecordWithFlags (cudaEventRecordExternal inside graphs).
 cudaError_t ms_init_f64(const Geom &g, int n, MsState *s, MsVectors<double2> v, const double2 *b, RedScratch rs,
@@ -155,6 +171,10 @@ cudaError_t ms_init_f32(const Geom &g, int n, MsState *s, MsVectors<float4> v, c
                         cudaStream_t st);
 cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, MsVectors<float4> v,
                         RedScratch rs, cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
+cudaError_t ms_init_half(const Geom &g, int n, MsState *s, MsVectorsH v, const float4 *b, RedScratch rs,
+                         cudaStream_t st);
+cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, MsVectorsH v, RedScratch rs,
+                         cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
 
 // Process-wide count of kernel launches issued by the library (instrumentation).
 void count_launches(long n);

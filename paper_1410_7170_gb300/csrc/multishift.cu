@@ -106,10 +106,12 @@ struct ShiftFin {
 // t = gamma5 D_W(m) p0 ; reduce ||t||^2, ||p0||^2
 template <typename R, typename LT, typename ST>
 __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, const LT *__restrict__ U, R m4, MsState *s,
-                                                 const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs) {
+                                                 const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs,
+                                                 int spb) {
     if (s->done) return;
     double v[2] = {0.0, 0.0};
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
+    const bool lane_has_sites = threadIdx.x < spb;
+    for (int k = blockIdx.x * spb + threadIdx.x; lane_has_sites && k < g.V; k += gridDim.x * spb) {
         int p, i;
         site_of_thread(k, p, i);
         cpx<R> hop[12], own[12], res[12];
@@ -134,11 +136,12 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, co
 template <typename R, typename LT, typename ST>
 __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r(Geom g, const LT *__restrict__ U, R m4, MsState *s,
                                                  const ST *__restrict__ t, const ST *__restrict__ p0,
-                                                 ST *__restrict__ r, RedScratch rs) {
+                                                 ST *__restrict__ r, RedScratch rs, int spb) {
     if (s->done) return;
     const R alpha = (R)s->alpha, sig0 = (R)s->sigma[0];
     double v[1] = {0.0};
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
+    const bool lane_has_sites = threadIdx.x < spb;
+    for (int k = blockIdx.x * spb + threadIdx.x; lane_has_sites && k < g.V; k += gridDim.x * spb) {
         int p, i;
         site_of_thread(k, p, i);
         cpx<R> hop[12], own[12], res[12], pp[12], rv[12];
@@ -362,6 +365,84 @@ inline int stream_grid(long n) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// ---- FP16-stored shifted directions (one thread per site: the FP16 words share a norm)
+// y += sum_l w_l a^l p_l ; p_l = zeta_l r + b^l p_l, with p_0 in FP32 and p_l (l >= 1)
+// in FP16; the last block retires finished shifts as k_ms_shifts does.
+__global__ void __launch_bounds__(kBlock) k_ms_shifts_half(Geom g, MsState *s, MsVectorsH v, unsigned *counter) {
+    __shared__ float sw[kMaxPoles], sz[kMaxPoles], sb[kMaxPoles];
+    __shared__ int sidx[kMaxPoles];
+    __shared__ int sact, sdone;
+    if (threadIdx.x == 0) {
+        sdone = s->done;
+        int na = 0;
+        if (sdone != 1)
+            for (int l = 0; l < s->n; l++)
+                if (s->active[l]) {
+                    sidx[na] = l;
+                    sw[na] = (float)(s->w[l] * s->alpha_l[l]);
+                    sz[na] = (float)s->zeta[l];
+                    sb[na] = (float)s->beta_l[l];
+                    na++;
+                }
+        sact = na;
+    }
+    __syncthreads();
+    if (sdone == 1) return;
+    const int na = sact;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
+        const int p = k >= g.Vh, i = k - p * g.Vh;   // no neighbours: plain parity-major order
+        cpx<float> rv[12], yv[12], pv[12];
+        load_spinor<float>(v.r, g.Vh, p, i, rv);
+        load_spinor<float>(v.y, g.Vh, p, i, yv);
+        for (int a = 0; a < na; a++) {
+            const int l = sidx[a];
+            const float wl = sw[a], zl = sz[a], bl = sb[a];
+            if (l == 0) {
+                load_spinor<float>(v.p0, g.Vh, p, i, pv);
+            } else {
+                load_spinor<float>(HalfSpinorC{v.ph + (size_t)(l - 1) * v.words_h, v.pn + (size_t)(l - 1) * g.V},
+                                   g.Vh, p, i, pv);
+            }
+#pragma unroll
+            for (int c = 0; c < 12; c++) {
+                yv[c] = yv[c] + wl * pv[c];
+                pv[c] = zl * rv[c] + bl * pv[c];
+            }
+            if (l == 0) store_spinor<float>(v.p0, g.Vh, p, i, pv);
+            else store_spinor<float>(HalfSpinor{v.ph + (size_t)(l - 1) * v.words_h, v.pn + (size_t)(l - 1) * g.V},
+                                     g.Vh, p, i, pv);
+        }
+        store_spinor<float>(v.y, g.Vh, p, i, yv);
+    }
+    if (grid_last_block(counter)) {
+        for (int l = threadIdx.x; l < s->n; l += blockDim.x)
+            if (s->active[l] == 2) s->active[l] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0 && s->done == 2) s->done = 1;
+    }
+}
+
+// r = y = p_0 = b in FP32, p_l = b in FP16 (l >= 1) ; ||b||^2
+__global__ void k_ms_init_half(Geom g, MsState *s, MsVectorsH v, const float4 *__restrict__ b, int n, RedScratch rs) {
+    double acc[1] = {0.0};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
+        const int p = k >= g.Vh, i = k - p * g.Vh;
+        cpx<float> bv[12];
+        load_spinor<float>(b, g.Vh, p, i, bv);
+        store_spinor<float>(v.r, g.Vh, p, i, bv);
+        store_spinor<float>(v.y, g.Vh, p, i, bv);
+        store_spinor<float>(v.p0, g.Vh, p, i, bv);
+        for (int l = 1; l < n; l++)
+            store_spinor<float>(HalfSpinor{v.ph + (size_t)(l - 1) * v.words_h, v.pn + (size_t)(l - 1) * g.V}, g.Vh, p,
+                                i, bv);
+        float a = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; c++) a += norm2(bv[c]);
+        acc[0] += (double)a;
+    }
+    grid_reduce<1>(acc, rs, InitFin{s});
+}
+
 template <typename R, typename LT, typename ST>
 cudaError_t ms_iter_t(const Geom &g, const LT *U, R m0, MsState *s, MsVectors<ST> v, RedScratch rs,
                       cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
@@ -371,10 +452,10 @@ cudaError_t ms_iter_t(const Geom &g, const LT *U, R m0, MsState *s, MsVectors<ST
     cudaError_t e;
     if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
     if (tps == 4) k_ms_q4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
-    else k_ms_q<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
+    else k_ms_q<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs, ls.spb);
     if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
     if (tps == 4) k_ms_r4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
-    else k_ms_r<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
+    else k_ms_r<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs, ls.spb);
     if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
     k_ms_shifts<ST><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.y, v.p, v.stride, v.stride, rs.counter);
     if (ev && (e = cudaEventRecordWithFlags(ev[3], st, ev_flags)) != cudaSuccess) return e;
@@ -405,4 +486,27 @@ cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, Ms
     return ms_iter_t<float, float4, float4>(g, U, m0, s, v, rs, st, ev, ev_flags);
 }
 
+}  // namespace ovl
+
+namespace ovl {
+cudaError_t ms_init_half(const Geom &g, int n, MsState *s, MsVectorsH v, const float4 *b, RedScratch rs,
+                         cudaStream_t st) {
+    k_ms_init_half<<<red_grid(g.V), kBlock, 0, st>>>(g, s, v, b, n, rs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, MsVectorsH v, RedScratch rs,
+                         cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
+    const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<float>::value, kMaxRedBlocks);
+    cudaError_t e;
+    if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
+    k_ms_q<float, float4, float4><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + 4.f, s, v.p0, v.t, rs, ls.spb);
+    if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
+    k_ms_r<float, float4, float4><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + 4.f, s, v.t, v.p0, v.r, rs, ls.spb);
+    if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
+    k_ms_shifts_half<<<balanced_shape(g.V, g.nsm, 2, 1 << 30).grid, kBlock, 0, st>>>(g, s, v, rs.counter);
+    if (ev && (e = cudaEventRecordWithFlags(ev[3], st, ev_flags)) != cudaSuccess) return e;
+    count_launches(3);
+    return cudaGetLastError();
+}
 }  // namespace ovl

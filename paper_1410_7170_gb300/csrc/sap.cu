@@ -25,6 +25,11 @@ namespace ovl {
 
 namespace {
 
+// Resident CTAs per SM the block kernel is compiled for: FP32 blocks (98 KB of shared
+// memory for 4^4 sites) fit two per SM at 128 registers; FP64 blocks (196 KB) fit one.
+template <typename R> struct SapMinBlocks { static constexpr int value = 2; };
+template <> struct SapMinBlocks<double> { static constexpr int value = 1; };
+
 // Shared-memory layout (R = arithmetic type): spinor s [24][nb], links [4][18][nb].
 template <typename R>
 struct SapSmem {
@@ -103,19 +108,35 @@ __device__ __forceinline__ void block_sum_sh(double v[3], double *sh) {
     __syncthreads();
 }
 
-template <typename R, typename LT, typename ST>
-__global__ void k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const ST *__restrict__ r, ST *x, R m4,
-                            int colour, int mr_iters) {
+// One CTA per block of the given colour.
+//   RES = false: the block residual is r_B = v_B (x = 0 everywhere before this sweep);
+//   RES = true:  r_B = v_B - (D_W x)_B is formed here from global x (own sites and the
+//                neighbours across the block faces, which have the other colour and are
+//                not written during this launch).
+// colour_grid = true: the grid holds only the blocks of this colour (blocks per direction
+// all even); otherwise it holds all blocks and the other colour's CTAs return at once.
+template <typename R, typename LT, typename ST, bool RES>
+__global__ void __launch_bounds__(kBlock, SapMinBlocks<R>::value) k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const ST *__restrict__ v, ST *x, R m4,
+                            int colour, int mr_iters, bool colour_grid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sh[3];
     const int nb = sg.nb;
     // block coordinates of this CTA
     int B[4], rem = blockIdx.x;
-    B[3] = rem % sg.nblk[3]; rem /= sg.nblk[3];
-    B[2] = rem % sg.nblk[2]; rem /= sg.nblk[2];
-    B[1] = rem % sg.nblk[1];
-    B[0] = rem / sg.nblk[1];
-    if (((B[0] + B[1] + B[2] + B[3]) & 1) != colour) return;   // uniform over the CTA
+    if (colour_grid) {
+        const int h3 = sg.nblk[3] / 2;
+        const int b3h = rem % h3; rem /= h3;
+        B[2] = rem % sg.nblk[2]; rem /= sg.nblk[2];
+        B[1] = rem % sg.nblk[1];
+        B[0] = rem / sg.nblk[1];
+        B[3] = 2 * b3h + ((B[0] + B[1] + B[2] + colour) & 1);
+    } else {
+        B[3] = rem % sg.nblk[3]; rem /= sg.nblk[3];
+        B[2] = rem % sg.nblk[2]; rem /= sg.nblk[2];
+        B[1] = rem % sg.nblk[1];
+        B[0] = rem / sg.nblk[1];
+        if (((B[0] + B[1] + B[2] + B[3]) & 1) != colour) return;   // uniform over the CTA
+    }
     R *s = reinterpret_cast<R *>(smem_raw);
     R *u = s + 24 * nb;
     // the CTA is padded to whole warps; threads t >= nb hold no site but join the reductions
@@ -152,7 +173,17 @@ __global__ void k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const 
         res[c] = cpx<R>{0, 0};
         q[c] = cpx<R>{0, 0};
     }
-    if (act) load_spinor<R>(r, g.Vh, p, i, res);
+    if (act) {
+        load_spinor<R>(v, g.Vh, p, i, res);
+        if (RES) {   // res = v - D_W x at this site
+            cpx<R> hop[12], own[12], dx[12];
+            wilson_hop<R>(g, U, x, p, i, hop);
+            load_spinor<R>(x, g.Vh, p, i, own);
+            wilson_combine<R>(m4, own, hop, dx);
+#pragma unroll
+            for (int c = 0; c < 12; c++) res[c] = res[c] - dx[c];
+        }
+    }
     for (int it = 0; it < mr_iters; it++) {
         if (act) sm_store_sp(s, nb, t, res);
         __syncthreads();
@@ -175,6 +206,7 @@ __global__ void k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const 
             res[c] = res[c] - alpha * q[c];
         }
     }
+    __syncthreads();   // every thread of the CTA has finished reading x before any writes it
     if (!act) return;
     cpx<R> xv[12];
     load_spinor<R>(x, g.Vh, p, i, xv);
@@ -191,31 +223,51 @@ static cudaError_t sap_t(const Geom &g, const SapGeom &sg, const LT *U, const ST
                          cudaError_t (*wil)(const Geom &, const LT *, const ST *, ST *, R, int, R, const ST *, R,
                                             cudaStream_t)) {
     const size_t smem = (size_t)sg.nb * (24 + 4 * 18) * sizeof(R);
-    static size_t attr_set[2] = {0, 0};   // dynamic shared memory granted so far, per precision
+    static size_t attr_set[2][2] = {{0, 0}, {0, 0}};   // dynamic shared memory granted, per precision/variant
     const int which = sizeof(R) == 8;
-    if (smem > 48 * 1024 && smem > attr_set[which]) {
-        cudaError_t e = cudaFuncSetAttribute(k_sap_block<R, LT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return e;
+    if (smem > 48 * 1024) {
+        cudaError_t e;
+        if (smem > attr_set[which][0]) {
+            if ((e = cudaFuncSetAttribute(k_sap_block<R, LT, ST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess) {
+                cudaGetLastError();
+                return e;
+            }
+            attr_set[which][0] = smem;
         }
-        attr_set[which] = smem;
+        if (smem > attr_set[which][1]) {
+            if ((e = cudaFuncSetAttribute(k_sap_block<R, LT, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess) {
+                cudaGetLastError();
+                return e;
+            }
+            attr_set[which][1] = smem;
+        }
     }
     cudaError_t e = cudaMemsetAsync(x, 0, (size_t)g.V * 24 * sizeof(R), st);
     if (e != cudaSuccess) return e;
     const int nblocks = sg.nblk[0] * sg.nblk[1] * sg.nblk[2] * sg.nblk[3];
+    // with an even number of blocks in every direction the colours alternate across every
+    // face (also through the periodic boundary): one colour's blocks can form their own
+    // residuals in place and the grid can hold only that colour
+    const bool even = !(sg.nblk[0] & 1) && !(sg.nblk[1] & 1) && !(sg.nblk[2] & 1) && !(sg.nblk[3] & 1);
+    const int grid = even ? nblocks / 2 : nblocks;
+    const int threads = (sg.nb + 31) / 32 * 32;
     bool x_zero = true;
     for (int cyc = 0; cyc < cycles; cyc++) {
         for (int colour = 0; colour < 2; colour++) {
-            const ST *res = v;
-            if (!x_zero) {
-                // r = v - D_W x
+            if (x_zero) {
+                k_sap_block<R, LT, ST, false><<<grid, threads, smem, st>>>(g, sg, U, v, x, m0 + (R)4, colour,
+                                                                           mr_iters, even);
+            } else if (even) {
+                k_sap_block<R, LT, ST, true><<<grid, threads, smem, st>>>(g, sg, U, v, x, m0 + (R)4, colour,
+                                                                          mr_iters, even);
+            } else {
+                // r = v - D_W x on the whole lattice, then the block solves from r
                 if ((e = wil(g, U, x, r, m0, 0, (R)-1, v, (R)1, st)) != cudaSuccess) return e;
-                res = r;
+                k_sap_block<R, LT, ST, false><<<grid, threads, smem, st>>>(g, sg, U, r, x, m0 + (R)4, colour,
+                                                                           mr_iters, even);
             }
-            k_sap_block<R, LT, ST><<<nblocks, (sg.nb + 31) / 32 * 32, smem, st>>>(g, sg, U, res, x, m0 + (R)4,
-                                                                                 colour, mr_iters);
             count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             x_zero = false;

@@ -69,6 +69,8 @@ struct Ctx {
     MsState *ms64_state = nullptr, *ms32_state = nullptr;
     MsVectors<double2> ms64{};
     MsVectors<float4> ms32{};
+    MsVectorsH msh{};
+    MsState *msh_state = nullptr;
     GraphSlot graphs[4];
     // instrumentation
     bool prof = false;
@@ -99,12 +101,15 @@ struct Ctx {
     ovl_status import_vec(const double *src, double2 *dst);
     ovl_status export_vec(const double2 *src, double *dst);
     ovl_status ms_setup(MsState *d_state, double tol);
+    // which: instrumentation class (0 FP64, 1 FP32/FP16); slot: CUDA-graph slot;
+    // shift_bytes: algorithmic bytes per site of one shift update (read + write of p_l)
     template <typename Iter>
-    ovl_status ms_run(MsState *d_state, int which, Iter iter_fn, int *iters_out);
+    ovl_status ms_run(MsState *d_state, int which, int slot, double shift_bytes, Iter iter_fn, int *iters_out);
     ovl_status sign64(const double2 *b, double2 *out, double tol, int mode);
     ovl_status sign32(const float4 *b, float4 *out, double tol, int mode);
     ovl_status ensure_ms64();
     ovl_status ensure_ms32();
+    ovl_status ensure_msh();
     ovl_status lanczos_bounds(double *lmin, double *lmax);
     ovl_status sigma_min_estimate(double *smin);
     ovl_status set_zolotarev();

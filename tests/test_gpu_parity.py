@@ -181,6 +181,7 @@ def test_gmres_solve_matches_dense_lu(c1):
     (ovl.OVL_PREC_WILSON, ovl.OVL_MIXED_FP32, 4),
     (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_FP32, 1),
     (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_FP32, 4),
+    (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_HALF, 1),
 ])
 def test_preconditioned_solves_match_dense_lu(c1, precond, precision, tps):
     dims, U, rho, DN, S, aw = c1
@@ -264,4 +265,23 @@ def test_autotuner_reports_a_choice():
     t = op.tuning()
     assert t["tps64"] in (1, 4) and t["tps32"] in (1, 4)
     assert all(m > 0 for m in t["ms"])
+    op.close()
+
+
+def test_config4_half_storage_full_size():
+    """32^3 x 64, 3-stout links, mu = 0.01, one Z2 source: FP16-stored inner multishift,
+    FP64 outer FGMRES, tol 1e-10. The oracle cannot solve at this size; the check is the
+    true residual through the FP64 D_N (itself pinned to the oracle at smaller volumes)."""
+    dims = (64, 32, 32, 32)
+    U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1004, stout_steps=3)).cuda()
+    b = torch.from_numpy(synth.rhs_z2(dims, 2004)).cuda()
+    op = ovl.Overlap(U, dims, 1.0, 0.01, ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE,
+                                                            precision=ovl.OVL_MIXED_HALF))
+    x = torch.zeros_like(b)
+    st, stats = op.ovl_solve(x, b, 1, 1e-10)
+    r = torch.empty_like(b)
+    op.ovl_apply(r, x, 1e-13)
+    res = ((b - r).norm() / b.norm()).item()
+    assert res < 2e-10, (res, stats)
+    assert stats["ms_iters_low"] > 0
     op.close()
