@@ -144,6 +144,15 @@ ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, double m0, dou
  * (ms[0..3] = FP64 x1, FP64 x4, FP32 x1, FP32 x4; zeros when forced). Nullable outputs. */
 ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, float *ms);
 
+/* out_k = D_W(m0) in_k for k < n_rhs (n_rhs vectors back to back), with the multi-RHS
+ * stencil: blocks of up to 12 right-hand sides per launch share every link load. */
+ovl_status wilson_apply_n(ovl_ctx *ctx, double *out, const double *in, int n_rhs, double m0);
+
+/* out_k ~= D_N in_k for k < n_rhs (Eq. overlap_def), all right-hand sides of a block of up
+ * to 12 evaluated by one lock-step FP64 multishift CG on the multi-RHS stencil; sign accuracy
+ * tol for each. */
+ovl_status ovl_apply_n(ovl_ctx *ctx, double *out, const double *in, int n_rhs, double tol);
+
 /* out ~= sign(Q) in, Q = Gamma5 D_W(m0_ker), to relative accuracy tol (>= 1e-14):
  * Zolotarev rational approximation + FP64 multishift CG (Sec. 2, Eq. overlap_def). */
 ovl_status sign_apply(ovl_ctx *ctx, double *out, const double *in, double tol);
@@ -195,6 +204,10 @@ typedef struct {
  * precision 0 = FP64, 1 = FP32. *ms = average milliseconds per launch. Algorithmic traffic
  * of one launch: 96 reals per site (4 links x 12, the input and the output spinor). */
 ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms);
+
+/* As ovl_dslash_time for the multi-RHS stencil applied to nrhs (1..12) right-hand sides per
+ * launch; *ms per launch (nrhs full-lattice applications). */
+ovl_status ovl_dslash_time_n(ovl_ctx *ctx, int precision, int nrhs, int reps, double *ms);
 
 /* on = 1 enables event timing (allocates a small history buffer), 0 disables it. */
 ovl_status ovl_prof_enable(ovl_ctx *ctx, int on);

@@ -74,7 +74,8 @@ class ovl_prof(ctypes.Structure):
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
-           "wilson_solve", "ovl_tuning", "wilson_apply_noalloc", "ovl_dslash_time"]
+           "wilson_solve", "ovl_tuning", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
+           "ovl_apply_n", "ovl_dslash_time_n"]
 
 _lib = None
 
@@ -104,6 +105,9 @@ def lib():
         L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
         L.wilson_apply_noalloc.argtypes = [P, P, P, P, D, I_, P]
         L.ovl_dslash_time.argtypes = [P, I_, I_, ctypes.POINTER(D)]
+        L.wilson_apply_n.argtypes = [P, P, P, I_, D]
+        L.ovl_apply_n.argtypes = [P, P, P, I_, D]
+        L.ovl_dslash_time_n.argtypes = [P, I_, I_, I_, ctypes.POINTER(D)]
         for name in EXPORTS:
             if name not in ("ovl_last_error",):
                 getattr(L, name).restype = I_
@@ -227,6 +231,22 @@ def ovl_dslash_time(ctx, precision, reps=20):
     return ms.value
 
 
+def wilson_apply_n(ctx, out, inp, n_rhs, m0):
+    _check(lib().wilson_apply_n(ctx, _ptr(out, True), _ptr(inp), int(n_rhs), float(m0)), ctx)
+    return out
+
+
+def ovl_apply_n(ctx, out, inp, n_rhs, tol):
+    _check(lib().ovl_apply_n(ctx, _ptr(out, True), _ptr(inp), int(n_rhs), float(tol)), ctx)
+    return out
+
+
+def ovl_dslash_time_n(ctx, precision, nrhs, reps=20):
+    ms = ctypes.c_double()
+    _check(lib().ovl_dslash_time_n(ctx, int(precision), int(nrhs), int(reps), ctypes.byref(ms)), ctx)
+    return ms.value
+
+
 def ovl_info(ctx):
     vals = [ctypes.c_double() for _ in range(7)]
     _check(lib().ovl_info(ctx, *[ctypes.byref(v) for v in vals]), ctx)
@@ -286,6 +306,15 @@ class Overlap:
 
     def dslash_time(self, precision, reps=20):
         return ovl_dslash_time(self.ctx, precision, reps)
+
+    def dslash_time_n(self, precision, nrhs, reps=20):
+        return ovl_dslash_time_n(self.ctx, precision, nrhs, reps)
+
+    def wilson_apply_n(self, out, inp, n_rhs, m0):
+        return wilson_apply_n(self.ctx, out, inp, n_rhs, m0)
+
+    def ovl_apply_n(self, out, inp, n_rhs, tol):
+        return ovl_apply_n(self.ctx, out, inp, n_rhs, tol)
 
     def prof_enable(self, on=True):
         ovl_prof_enable(self.ctx, on)

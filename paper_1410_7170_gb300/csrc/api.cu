@@ -385,6 +385,168 @@ ovl_status Ctx::ensure_ms64() {
     ms64.stride = words;
     return OVL_OK;
 }
+// ---- several right-hand sides
+ovl_status Ctx::ensure_batch() {
+    Ctx *c = this;
+    if (msb_state) return OVL_OK;
+    void *buf;
+    ST(alloc(&buf, sizeof(MsState) * kMaxBatch));
+    msb_state = (MsState *)buf;
+    ST(alloc(&buf, sizeof(double) * (size_t)kMaxBatch * 2 * kMaxRedBlocks + 256));
+    rsb.partials = (double *)buf;
+    rsb.counter = (unsigned *)((char *)buf + sizeof(double) * (size_t)kMaxBatch * 2 * kMaxRedBlocks);
+    ST(alloc(&buf, sizeof(unsigned) * kMaxBatch));
+    bcounters = (unsigned *)buf;
+    CK(cudaMemsetAsync(rsb.counter, 0, sizeof(unsigned), stream));
+    CK(cudaMemsetAsync(bcounters, 0, sizeof(unsigned) * kMaxBatch, stream));
+    CK(cudaMallocHost(&h_pinned_b, sizeof(MsState) * kMaxBatch + 4096));
+    h_msb = (MsState *)h_pinned_b;
+    h_msb_small = (int *)((char *)h_pinned_b + sizeof(MsState) * kMaxBatch);
+    return OVL_OK;
+}
+
+// Lock-step multishift solves of nrhs right-hand sides (tolerance tol[y] each); the
+// host polls the first four words (n, iter, done, status) of every state per chunk.
+template <typename ST, typename Init, typename Iter>
+ovl_status Ctx::msb_run(int nrhs, const double *tol, int slot, Init init_fn, Iter iter_fn, long *iters_out) {
+    Ctx *c = this;
+    for (int y = 0; y < nrhs; y++) {
+        MsState &s = h_msb[y];
+        memset(&s, 0, sizeof(MsState));
+        s.n = npole;
+        s.tol = tol[y];
+        s.alpha_prev = 1.0;
+        for (int l = 0; l < npole; l++) {
+            s.sigma[l] = lam_min * lam_min * zc[l];
+            s.w[l] = za[l] * lam_min * lam_min;
+            s.crit[l] = npole * zd0 * fabs(za[l]) / (2.0 * sqrt(zc[l]));
+            s.zeta[l] = 1.0;
+            s.zeta_prev[l] = 1.0;
+            s.active[l] = 1;
+        }
+        if (!(tol[y] > 0)) s.done = 1;   // a right-hand side that needs no work this time
+    }
+    CK(cudaMemcpyAsync(msb_state, h_msb, sizeof(MsState) * nrhs, cudaMemcpyHostToDevice, stream));
+    CK(init_fn());
+    const int chunk = std::min(p.check_every, kMaxChunk);
+    GraphSlot &gs = graphs[slot];
+    if (gs.exec && (gs.nrhs != nrhs || gs.chunk != chunk)) {
+        cudaGraphExecDestroy(gs.exec);
+        gs.exec = nullptr;
+    }
+    int done_iters = 0;
+    while (true) {
+        if (p.use_graphs) {
+            if (!gs.exec) {
+                cudaGraph_t graph;
+                set_launch_counting(false);
+                CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaSuccess;
+                for (int k = 0; k < chunk && ce == cudaSuccess; k++) ce = iter_fn();
+                cudaError_t ee = cudaStreamEndCapture(stream, &graph);
+                set_launch_counting(true);
+                CK(ce);
+                CK(ee);
+                cudaError_t ie = cudaGraphInstantiate(&gs.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                CK(ie);
+                gs.nrhs = nrhs;
+                gs.chunk = chunk;
+            }
+            CK(cudaGraphLaunch(gs.exec, stream));
+            count_launches(3L * chunk);
+        } else {
+            for (int k = 0; k < chunk; k++) CK(iter_fn());
+        }
+        done_iters += chunk;
+        CK(cudaMemcpy2DAsync(h_msb_small, 4 * sizeof(int), msb_state, sizeof(MsState), 4 * sizeof(int), nrhs,
+                             cudaMemcpyDeviceToHost, stream));
+        ST(sync());
+        bool all = true;
+        long itmax = 0;
+        for (int y = 0; y < nrhs; y++) {
+            const int *h = h_msb_small + 4 * y;
+            if (h[3]) {
+                err = "batched multishift CG breakdown (non-finite or non-positive scalar)";
+                return OVL_EBREAKDOWN;
+            }
+            all = all && h[2];
+            itmax = std::max(itmax, (long)h[1]);
+        }
+        if (all) {
+            *iters_out = itmax;
+            return OVL_OK;
+        }
+        if (itmax >= p.max_ms_iter || done_iters > p.max_ms_iter + chunk) {
+            *iters_out = itmax;
+            err = "batched multishift CG reached max_ms_iter";
+            return OVL_ENOCONV;
+        }
+    }
+}
+
+ovl_status Ctx::sign64_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode) {
+    Ctx *c = this;
+    ST(ensure_batch());
+    if (!msb64.p || msb64_cap < nrhs) {   // sized to the batch (grown when a larger one comes)
+        if (msb64.p) {
+            cudaFree(msb64.r);
+            allocs.erase(std::find(allocs.begin(), allocs.end(), (void *)msb64.r));
+        }
+        const long words = (long)g.V * 12;
+        void *buf;
+        ST(alloc(&buf, (size_t)words * sizeof(double2) * nrhs * (npole + 3)));
+        double2 *d = (double2 *)buf;
+        msb64.r = d;
+        msb64.t = d + words * nrhs;
+        msb64.y = d + 2 * words * nrhs;
+        msb64.p = d + 3 * words * nrhs;
+        msb64.stride = words;
+        msb64_cap = nrhs;
+    }
+    long iters = 0;
+    auto init = [&]() { return msb_init_f64(g, nrhs, npole, msb_state, msb64, b, rsb, stream); };
+    auto it = [&]() { return msb_iter_f64(g, U64, m0_ker, nrhs, npole, msb_state, msb64, rsb, bcounters, stream); };
+    ST((msb_run<double2>(nrhs, tol, 3, init, it, &iters)));
+    stat_ms64 += iters * nrhs;
+    const double sc = zd0 / lam_min;
+    CK(wilson_batch_f64(g, U64, msb64.y, out, msb64.stride, nrhs, m0_ker, mode == 0, sc, mode == 1 ? b : nullptr,
+                        rho, stream));
+    return OVL_OK;
+}
+
+ovl_status Ctx::sign32_batch(const float4 *b, float4 *out, int nrhs, const double *tol, int mode) {
+    Ctx *c = this;
+    ST(ensure_batch());
+    if (!msb32.p || msb32_cap < nrhs) {
+        if (msb32.p) {
+            cudaFree(msb32.r);
+            allocs.erase(std::find(allocs.begin(), allocs.end(), (void *)msb32.r));
+        }
+        const long words = (long)g.V * 6;
+        void *buf;
+        ST(alloc(&buf, (size_t)words * sizeof(float4) * nrhs * (npole + 3)));
+        float4 *d = (float4 *)buf;
+        msb32.r = d;
+        msb32.t = d + words * nrhs;
+        msb32.y = d + 2 * words * nrhs;
+        msb32.p = d + 3 * words * nrhs;
+        msb32.stride = words;
+        msb32_cap = nrhs;
+    }
+    long iters = 0;
+    auto init = [&]() { return msb_init_f32(g, nrhs, npole, msb_state, msb32, b, rsb, stream); };
+    auto it = [&]() {
+        return msb_iter_f32(g, U32, (float)m0_ker, nrhs, npole, msb_state, msb32, rsb, bcounters, stream);
+    };
+    ST((msb_run<float4>(nrhs, tol, 4, init, it, &iters)));
+    stat_ms32 += iters * nrhs;
+    const float sc = (float)(zd0 / lam_min);
+    CK(wilson_batch_f32(g, U32, msb32.y, out, msb32.stride, nrhs, (float)m0_ker, mode == 0, sc,
+                        mode == 1 ? b : nullptr, (float)rho, stream));
+    return OVL_OK;
+}
+
 ovl_status Ctx::ensure_msh() {
     if (msh.ph) return OVL_OK;
     if (!msh_state) {
@@ -684,13 +846,14 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
         CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
-    // pinned host scratch
-    CK(cudaMallocHost(&c->h_pinned, 1 << 16));
+    // pinned host scratch: scalars, flags, multishift state copies
+    CK(cudaMallocHost(&c->h_pinned, (size_t)kScal * sizeof(double) + (1 << 16)));
     c->h_scal = (double *)c->h_pinned;
-    c->h_flag = (int *)((char *)c->h_pinned + 4096);
-    c->h_ms_small = (int *)((char *)c->h_pinned + 8192);
-    c->h_ms = (MsState *)((char *)c->h_pinned + 16384);
-    c->h_hist = (int *)((char *)c->h_pinned + 32768);
+    char *hp = (char *)c->h_pinned + (size_t)kScal * sizeof(double);
+    c->h_flag = (int *)hp;
+    c->h_ms_small = (int *)(hp + 4096);
+    c->h_ms = (MsState *)(hp + 8192);
+    c->h_hist = (int *)(hp + 32768);
     c->launch_mark = launches_total();
     // device scratch
     void *buf;
@@ -699,7 +862,7 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
     c->rs.counter = (unsigned *)((char *)buf + sizeof(double) * kMaxRedValues * kMaxRedBlocks);
     c->d_flag = (int *)((char *)buf + sizeof(double) * kMaxRedValues * kMaxRedBlocks + 256);
     CK(cudaMemsetAsync(buf, 0, sizeof(double) * kMaxRedValues * kMaxRedBlocks + 4096, c->stream));
-    ST(c->alloc(&buf, 4096));
+    ST(c->alloc(&buf, (size_t)kScal * sizeof(double)));
     c->d_scal = (double *)buf;
     ST(c->alloc(&buf, sizeof(MsState)));
     c->ms64_state = (MsState *)buf;
@@ -965,6 +1128,105 @@ extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, dou
     if (st != OVL_OK) {
         cudaGetLastError();
         c->err = "ovl_dslash_time: CUDA error";
+        return st;
+    }
+    *ms = t / reps;
+    return OVL_OK;
+}
+
+extern "C" ovl_status wilson_apply_n(ovl_ctx *ctx, double *out, const double *in, int n_rhs, double m0) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    if (n_rhs < 1 || !isfinite(m0)) {
+        c->err = "need n_rhs >= 1 and finite m0";
+        return OVL_EINVAL;
+    }
+    ST(c->ensure_batch());
+    if (!c->xbat) {   // staging for one block of right-hand sides (kept; reused by later calls)
+        const int cap = std::min(kMaxBatch, n_rhs);
+        void *buf;
+        ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2 * cap));
+        c->xbat = (double2 *)buf;
+        c->bbat = c->xbat + (size_t)cap * c->g.V * 12;
+        c->xbat_cap = cap;
+    }
+    const int blk = c->xbat_cap;
+    const long w = (long)c->g.V * 12;
+    for (int r0 = 0; r0 < n_rhs; r0 += blk) {
+        const int nb = std::min(blk, n_rhs - r0);
+        for (int y = 0; y < nb; y++) ST(c->import_vec(in + (size_t)(r0 + y) * c->n64, c->bbat + y * w));
+        CK(wilson_batch_f64(c->g, c->U64, c->bbat, c->xbat, w, nb, m0, 0, 1.0, nullptr, 0.0, c->stream));
+        for (int y = 0; y < nb; y++) ST(c->export_vec(c->xbat + y * w, out + (size_t)(r0 + y) * c->n64));
+    }
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_apply_n(ovl_ctx *ctx, double *out, const double *in, int n_rhs, double tol) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    ST(check_tol(c, tol));
+    if (n_rhs < 1) {
+        c->err = "n_rhs must be >= 1";
+        return OVL_EINVAL;
+    }
+    ST(c->ensure_batch());
+    if (!c->xbat) {   // staging for one block of right-hand sides (kept; reused by later calls)
+        const int cap = std::min(kMaxBatch, n_rhs);
+        void *buf;
+        ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2 * cap));
+        c->xbat = (double2 *)buf;
+        c->bbat = c->xbat + (size_t)cap * c->g.V * 12;
+        c->xbat_cap = cap;
+    }
+    const int blk = c->xbat_cap;
+    const long w = (long)c->g.V * 12;
+    double t[kMaxBatch];
+    for (int y = 0; y < kMaxBatch; y++) t[y] = tol;
+    for (int r0 = 0; r0 < n_rhs; r0 += blk) {
+        const int nb = std::min(blk, n_rhs - r0);
+        for (int y = 0; y < nb; y++) ST(c->import_vec(in + (size_t)(r0 + y) * c->n64, c->bbat + y * w));
+        ST(c->sign64_batch(c->bbat, c->xbat, nb, t, 1));
+        for (int y = 0; y < nb; y++) ST(c->export_vec(c->xbat + y * w, out + (size_t)(r0 + y) * c->n64));
+    }
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_dslash_time_n(ovl_ctx *ctx, int precision, int nrhs, int reps, double *ms) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !ms || reps < 1 || nrhs < 1 || nrhs > kMaxBatch || (precision != 0 && precision != 1)) return OVL_EINVAL;
+    void *buf;
+    const size_t bytes = (size_t)c->n64 * (precision == 0 ? 8 : 4) * nrhs * 2;
+    ST(c->alloc(&buf, bytes));
+    CK(cudaMemsetAsync(buf, 0, bytes, c->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    ovl_status st = OVL_OK;
+    for (int k = 0; k < 3 + reps && st == OVL_OK; k++) {
+        if (k == 3 && cudaEventRecord(e0, c->stream) != cudaSuccess) st = OVL_ECUDA;
+        cudaError_t e;
+        if (precision == 0) {
+            const long w = (long)c->g.V * 12;
+            e = wilson_batch_f64(c->g, c->U64, (const double2 *)buf, (double2 *)buf + w * nrhs, w, nrhs, c->m0_ker, 0,
+                                 1.0, nullptr, 0.0, c->stream);
+        } else {
+            const long w = (long)c->g.V * 6;
+            e = wilson_batch_f32(c->g, c->U32, (const float4 *)buf, (float4 *)buf + w * nrhs, w, nrhs,
+                                 (float)c->m0_ker, 0, 1.f, nullptr, 0.f, c->stream);
+        }
+        if (e != cudaSuccess) st = OVL_ECUDA;
+    }
+    float t = 0.f;
+    if (st == OVL_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        st = OVL_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), buf));
+    if (st != OVL_OK) {
+        cudaGetLastError();
+        c->err = "ovl_dslash_time_n: CUDA error";
         return st;
     }
     *ms = t / reps;

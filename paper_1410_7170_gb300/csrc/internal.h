@@ -176,6 +176,33 @@ cudaError_t ms_init_half(const Geom &g, int n, MsState *s, MsVectorsH v, const f
 cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, MsVectorsH v, RedScratch rs,
                          cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
 
+// ---------------------------------------------------------------- several right-hand sides
+constexpr int kMaxBatch = 12;   // right-hand sides per batch (threads 32 x nrhs per block)
+
+// out_y = a [gamma5] D_W(m0) in_y + b z_y for y < nrhs; vectors `stride` storage words apart.
+cudaError_t wilson_batch_f64(const Geom &g, const double2 *U, const double2 *in, double2 *out, long stride, int nrhs,
+                             double m0, int g5, double a, const double2 *z, double b, cudaStream_t st);
+cudaError_t wilson_batch_f32(const Geom &g, const float4 *U, const float4 *in, float4 *out, long stride, int nrhs,
+                             float m0, int g5, float a, const float4 *z, float b, cudaStream_t st);
+
+// Batched multishift vectors: per right-hand side y, r/t/y at base + y * stride and its
+// npole directions at p + (y * npole + l) * stride.
+template <typename ST>
+struct MsBatch {
+    ST *r, *t, *y, *p;
+    long stride;
+};
+// One state per right-hand side (st[y]); partial sums need nrhs * 2 * kMaxRedBlocks doubles;
+// counters: nrhs words, zero between launches.
+cudaError_t msb_init_f64(const Geom &g, int nrhs, int npole, MsState *st, MsBatch<double2> v, const double2 *b,
+                         RedScratch rs, cudaStream_t s);
+cudaError_t msb_init_f32(const Geom &g, int nrhs, int npole, MsState *st, MsBatch<float4> v, const float4 *b,
+                         RedScratch rs, cudaStream_t s);
+cudaError_t msb_iter_f64(const Geom &g, const double2 *U, double m0, int nrhs, int npole, MsState *st,
+                         MsBatch<double2> v, RedScratch rs, unsigned *counters, cudaStream_t s);
+cudaError_t msb_iter_f32(const Geom &g, const float4 *U, float m0, int nrhs, int npole, MsState *st,
+                         MsBatch<float4> v, RedScratch rs, unsigned *counters, cudaStream_t s);
+
 // Process-wide count of kernel launches issued by the library (instrumentation).
 void count_launches(long n);
 long launches_total();

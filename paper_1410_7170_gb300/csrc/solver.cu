@@ -12,8 +12,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <complex>
+#include <memory>
 #include <vector>
 
 #include "sap.h"
@@ -45,11 +47,12 @@ template <> struct Ops<double> {
     static cudaError_t axpby(Ctx *c, double a, const double *x, double b, double *y) {
         return dev_axpby(a, x, b, y, c->n64, c->stream);
     }
-    static cudaError_t multidot(Ctx *c, const double *base, int m, const double *w, double *out) {
-        return dev_multidot(base, c->n64, m, w, c->n64, out, c->d_md_part, c->stream);
+    // basis vectors k = 0..m-1 at base + k * stride (stride 0: consecutive vectors)
+    static cudaError_t multidot(Ctx *c, const double *base, int m, const double *w, double *out, long stride = 0) {
+        return dev_multidot(base, stride ? stride : c->n64, m, w, c->n64, out, c->d_md_part, c->stream);
     }
-    static cudaError_t multiaxpy(Ctx *c, const double *base, int m, const double *coef, double *w) {
-        return dev_multiaxpy(base, c->n64, m, coef, w, c->n64, c->stream);
+    static cudaError_t multiaxpy(Ctx *c, const double *base, int m, const double *coef, double *w, long stride = 0) {
+        return dev_multiaxpy(base, stride ? stride : c->n64, m, coef, w, c->n64, c->stream);
     }
     static cudaError_t wilson(Ctx *c, const double *in, double *out, double m0) {
         return wilson_f64(c->g, c->U64, (const double2 *)in, (double2 *)out, m0, 0, 1.0, nullptr, 0.0, c->stream);
@@ -66,11 +69,11 @@ template <> struct Ops<float> {
     static cudaError_t axpby(Ctx *c, double a, const float *x, double b, float *y) {
         return dev_axpby_f((float)a, x, (float)b, y, c->n64, c->stream);
     }
-    static cudaError_t multidot(Ctx *c, const float *base, int m, const float *w, double *out) {
-        return dev_multidot_f(base, c->n64, m, w, c->n64, out, c->d_md_part, c->stream);
+    static cudaError_t multidot(Ctx *c, const float *base, int m, const float *w, double *out, long stride = 0) {
+        return dev_multidot_f(base, stride ? stride : c->n64, m, w, c->n64, out, c->d_md_part, c->stream);
     }
-    static cudaError_t multiaxpy(Ctx *c, const float *base, int m, const double *coef, float *w) {
-        return dev_multiaxpy_f(base, c->n64, m, coef, w, c->n64, c->stream);
+    static cudaError_t multiaxpy(Ctx *c, const float *base, int m, const double *coef, float *w, long stride = 0) {
+        return dev_multiaxpy_f(base, stride ? stride : c->n64, m, coef, w, c->n64, c->stream);
     }
     static cudaError_t wilson(Ctx *c, const float *in, float *out, double m0) {
         return wilson_f32(c->g, c->U32, (const float4 *)in, (float4 *)out, (float)m0, 0, 1.f, nullptr, 0.f,
@@ -111,7 +114,7 @@ struct KrylovResult {
 
 // Upload complex coefficients (interleaved) to the device coefficient buffer.
 static ovl_status upload_coef(Ctx *c, const std::vector<cd> &v) {
-    double *h = c->h_scal + 256;
+    double *h = c->h_scal + kScal / 2;
     for (size_t k = 0; k < v.size(); k++) {
         h[2 * k] = v[k].real();
         h[2 * k + 1] = v[k].imag();
@@ -192,7 +195,7 @@ static ovl_status fgmres(Ctx *c, Krylov<T> &k, T *x, const T *b, double tol, int
                 CK(O::multidot(c, k.V, j + 1, k.w, c->d_scal));
                 CK(O::norm2(c, k.w, c->d_scal + 2 * (j + 1)));
                 double tmp[2 * 128 + 2];
-                ST(c->fetch(c->d_scal, 2 * (j + 1) + 1, tmp));
+                ST(c->fetch(c->d_scal, 2 * (j + 1) + 1, tmp));   // 2 (j + 1) + 1 <= 243 doubles
                 std::vector<cd> neg(j + 1);
                 double hsq = 0.0;
                 for (int i = 0; i <= j; i++) {
@@ -341,22 +344,53 @@ ovl_status wilson_solve_eo(Ctx *c, const double2 *b, double2 *x, double m0, doub
     return OVL_OK;
 }
 
+int batch_size_for(Ctx *c, int want);
+
 ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats) {
     const auto t0 = std::chrono::steady_clock::now();
     c->stat_ms64 = c->stat_ms32 = c->stat_prec = 0;
     c->stat_inner = 0;
     const bool flexible = c->p.precond != OVL_PREC_NONE;
-    ST(ensure_krylov<double>(c, c->kry_outer, c->p.restart, flexible));
-    if (!c->d_x) {
-        void *buf;
-        ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2));
-        c->d_x = (double2 *)buf;
-        c->d_b = c->d_x + c->g.V * 12;
-    }
     int outer_total = 0;
     double worst = 0.0;
     bool all_conv = true;
     const double tight = std::max(1e-14, std::min(c->p.sign_tol, 0.1 * tol));
+    if (n_rhs > 1 && c->p.rhs_block > 1) {
+        // several right-hand sides in lock-step batches sized to the free device memory
+        const int nbmax = batch_size_for(c, std::min(c->p.rhs_block, n_rhs));
+        if (!c->xbat || c->xbat_cap < nbmax) {
+            void *buf;
+            ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2 * nbmax));
+            c->xbat = (double2 *)buf;
+            c->bbat = c->xbat + (size_t)nbmax * c->g.V * 12;
+            c->xbat_cap = nbmax;
+        }
+        for (int r0 = 0; r0 < n_rhs; r0 += nbmax) {
+            const int nb = std::min(nbmax, n_rhs - r0);
+            for (int y = 0; y < nb; y++) {
+                ST(c->import_vec(b + (size_t)(r0 + y) * c->n64, c->bbat + (size_t)y * c->g.V * 12));
+                ST(c->import_vec(x + (size_t)(r0 + y) * c->n64, c->xbat + (size_t)y * c->g.V * 12));
+            }
+            int its;
+            double wr;
+            bool cv;
+            ST(solve_batch(c, c->xbat, c->bbat, nb, tol, &its, &wr, &cv));
+            outer_total += its;
+            worst = std::max(worst, wr);
+            all_conv = all_conv && cv;
+            for (int y = 0; y < nb; y++) ST(c->export_vec(c->xbat + (size_t)y * c->g.V * 12, x + (size_t)(r0 + y) * c->n64));
+        }
+        n_rhs = 0;   // done; fall through to the statistics
+    }
+    if (n_rhs > 0) {
+        ST(ensure_krylov<double>(c, c->kry_outer, c->p.restart, flexible));
+        if (!c->d_x) {
+            void *buf;
+            ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2));
+            c->d_x = (double2 *)buf;
+            c->d_b = c->d_x + c->g.V * 12;
+        }
+    }
     for (int r = 0; r < n_rhs; r++) {
         const double *br = b + (size_t)r * c->n64;
         double *xr = x + (size_t)r * c->n64;
@@ -408,6 +442,423 @@ ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, 
     if (!all_conv) {
         c->err = "ovl_solve: tolerance not reached within max_iter";
         return OVL_ENOCONV;
+    }
+    return OVL_OK;
+}
+
+// ====================================================================================
+// Several right-hand sides in lock-step.
+//
+// fgmres_batch runs nb independent FGMRES(m) iterations side by side: every basis entry
+// holds nb vectors back to back, so the operator and the preconditioner are applied to
+// all systems in one batched call (one multi-RHS stencil per application), while each
+// system keeps its own Hessenberg matrix, Givens rotations, relaxation and stopping test.
+// A system that has converged is dropped from the Gram-Schmidt work and its operator
+// applications are skipped inside the batched calls (tolerance <= 0).
+// ====================================================================================
+namespace {
+
+// nb FP64 <-> FP32 internal spinors back to back
+cudaError_t spinor_d2f_n(Ctx *c, const double2 *a, float4 *b, int nb) {
+    for (int y = 0; y < nb; y++) {
+        cudaError_t e = spinor_d2f(c->g, a + (long)y * c->g.V * 12, b + (long)y * c->g.V * 6, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+cudaError_t spinor_f2d_n(Ctx *c, const float4 *a, double2 *b, int nb) {
+    for (int y = 0; y < nb; y++) {
+        cudaError_t e = spinor_f2d(c->g, a + (long)y * c->g.V * 6, b + (long)y * c->g.V * 12, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+// Zero the input rows of systems that are not iterating, so a nested batched solve
+// treats them as converged (zero right-hand side) and spends no work on them.
+template <typename T>
+cudaError_t zero_inactive(Ctx *c, T *in, int nb, const char *act) {
+    for (int y = 0; y < nb; y++)
+        if (!act[y]) {
+            cudaError_t e = cudaMemsetAsync(in + (long)y * c->n64, 0, c->n64 * sizeof(T), c->stream);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+template <typename T>
+ovl_status ensure_krylov_batch(Ctx *c, Krylov<T> &k, int &cap, int m, int nb) {
+    if (k.V && k.m == m && cap >= nb) return OVL_OK;
+    const long n = c->n64;
+    const int nvec = (2 * m + 1 + 2) * nb;
+    void *buf;
+    ST(c->alloc(&buf, (size_t)n * sizeof(T) * nvec));
+    T *b = (T *)buf;
+    k.V = b;
+    k.Z = b + (long)(m + 1) * nb * n;
+    k.w = k.Z + (long)m * nb * n;
+    k.r = k.w + (long)nb * n;
+    k.m = m;
+    k.flexible = true;
+    cap = nb;
+    return OVL_OK;
+}
+
+// matvec(in, out, rel[nb]): out_y = A in_y (rel[y] < 0: full accuracy; rel[y] = 2: skip y)
+// precond(in, out, active[nb]): out_y ~ A^{-1} in_y for active y
+template <typename T, typename MV, typename PC>
+ovl_status fgmres_batch(Ctx *c, Krylov<T> &k, int nb, T *x, const T *b, double tol, int maxit, bool x_zero,
+                        MV matvec, PC precond, int *iters, double *rel_out, bool *conv_out, bool verify) {
+    using O = Ops<T>;
+    const long n = c->n64;
+    const int m = k.m;
+    auto vec = [&](T *base, int j, int y) { return base + ((long)j * nb + y) * n; };
+    std::vector<double> bnorm(nb), rel(nb), beta(nb);
+    std::vector<char> active(nb, 1), conv(nb, 0);
+    double tmp[2 * 128 + 2];
+    for (int y = 0; y < nb; y++) {
+        CK(O::norm2(c, b + (long)y * n, c->d_scal + y));
+    }
+    ST(c->fetch(c->d_scal, nb, tmp));
+    for (int y = 0; y < nb; y++) bnorm[y] = sqrt(tmp[y]);
+    if (x_zero) CK(cudaMemsetAsync(x, 0, (size_t)nb * n * sizeof(T), c->stream));
+    bool xz = x_zero;
+    int its = 0;
+    std::vector<std::vector<cd>> H(nb), cs(nb), sn(nb), gv(nb);
+    for (int y = 0; y < nb; y++) {
+        H[y].assign((size_t)(m + 1) * m, cd(0));
+        cs[y].assign(m, cd(0));
+        sn[y].assign(m, cd(0));
+        gv[y].assign(m + 1, cd(0));
+        if (bnorm[y] == 0.0) {
+            active[y] = 0;
+            conv[y] = 1;
+        }
+    }
+    std::vector<double> relv(nb);
+    while (true) {
+        // R = B - A X for the active systems
+        if (xz) {
+            CK(cudaMemcpyAsync(k.r, b, (size_t)nb * n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+            for (int y = 0; y < nb; y++) relv[y] = active[y] ? -1.0 : 2.0;
+            ST(matvec(x, k.w, relv.data()));
+            CK(cudaMemcpyAsync(k.r, b, (size_t)nb * n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+            for (int y = 0; y < nb; y++)
+                if (active[y]) CK(O::axpby(c, -1.0, k.w + (long)y * n, 1.0, k.r + (long)y * n));
+        }
+        for (int y = 0; y < nb; y++) CK(O::norm2(c, k.r + (long)y * n, c->d_scal + y));
+        ST(c->fetch(c->d_scal, nb, tmp));
+        bool any = false;
+        for (int y = 0; y < nb; y++) {
+            if (!active[y]) continue;
+            beta[y] = sqrt(tmp[y]);
+            rel[y] = beta[y] / bnorm[y];
+            if (!std::isfinite(beta[y])) {
+                c->err = "batched Krylov solver: non-finite residual";
+                return OVL_EBREAKDOWN;
+            }
+            if (beta[y] <= tol * bnorm[y]) {
+                active[y] = 0;
+                conv[y] = 1;
+            } else {
+                any = true;
+            }
+        }
+        if (!any || its >= maxit) break;
+        for (int y = 0; y < nb; y++) {
+            std::fill(gv[y].begin(), gv[y].end(), cd(0));
+            gv[y][0] = beta[y];
+            if (active[y]) CK(O::axpby(c, 1.0 / beta[y], k.r + (long)y * n, 0.0, vec(k.V, 0, y)));
+            else CK(cudaMemsetAsync(vec(k.V, 0, y), 0, n * sizeof(T), c->stream));
+        }
+        std::vector<char> live = active;   // systems iterating in this cycle
+        int j = 0;
+        for (; j < m; j++) {
+            bool alive = false;
+            for (int y = 0; y < nb; y++) alive = alive || live[y];
+            if (!alive) break;
+            ST(precond(vec(k.V, j, 0), vec(k.Z, j, 0), live.data()));
+            for (int y = 0; y < nb; y++) relv[y] = live[y] ? std::abs(gv[y][j]) / bnorm[y] : 2.0;
+            ST(matvec(vec(k.Z, j, 0), k.w, relv.data()));
+            // Gram-Schmidt per system: one pass, a second when it cancels (always in FP64)
+            std::vector<std::vector<cd>> h1(nb, std::vector<cd>(j + 1)), h2(nb, std::vector<cd>(j + 1));
+            std::vector<double> hn(nb, 0.0);
+            std::vector<char> need2(nb, 0);
+            for (int pass = 0; pass < 2; pass++) {
+                int cnt = 0;
+                for (int y = 0; y < nb; y++) {
+                    if (!live[y] || (pass == 1 && !need2[y])) continue;
+                    CK(O::multidot(c, vec(k.V, 0, y), j + 1, k.w + (long)y * n, c->d_scal + cnt * (2 * (j + 1) + 1),
+                                   (long)nb * n));
+                    CK(O::norm2(c, k.w + (long)y * n, c->d_scal + cnt * (2 * (j + 1) + 1) + 2 * (j + 1)));
+                    cnt++;
+                }
+                if (!cnt) break;
+                std::vector<double> all((size_t)cnt * (2 * (j + 1) + 1));
+                if (all.size() > (size_t)kScal / 2) {
+                    c->err = "batched Krylov solver: scalar staging too small";
+                    return OVL_EINVAL;
+                }
+                ST(c->fetch(c->d_scal, (int)all.size(), all.data()));
+                cnt = 0;
+                for (int y = 0; y < nb; y++) {
+                    if (!live[y] || (pass == 1 && !need2[y])) continue;
+                    const double *t = all.data() + (size_t)cnt * (2 * (j + 1) + 1);
+                    std::vector<cd> &hh = pass == 0 ? h1[y] : h2[y];
+                    std::vector<cd> neg(j + 1);
+                    double hsq = 0.0;
+                    for (int i = 0; i <= j; i++) {
+                        hh[i] = cd(t[2 * i], t[2 * i + 1]);
+                        neg[i] = -hh[i];
+                        hsq += std::norm(hh[i]);
+                    }
+                    ST(upload_coef(c, neg));
+                    CK(O::multiaxpy(c, vec(k.V, 0, y), j + 1, c->d_coef, k.w + (long)y * n, (long)nb * n));
+                    ST(c->sync());   // the coefficient staging is reused by the next system
+                    const double ww = t[2 * (j + 1)];
+                    const double left = ww - hsq;
+                    if (pass == 0) {
+                        if (!O::kCgs2 && left > 0.1 * ww) hn[y] = sqrt(left);
+                        else need2[y] = 1;
+                    } else {
+                        hn[y] = sqrt(std::max(0.0, left));
+                    }
+                    cnt++;
+                }
+            }
+            for (int y = 0; y < nb; y++) {
+                if (!live[y]) continue;
+                std::vector<cd> &Hy = H[y];
+                for (int i = 0; i <= j; i++) Hy[(size_t)i * m + j] = h1[y][i] + (need2[y] ? h2[y][i] : cd(0));
+                Hy[(size_t)(j + 1) * m + j] = hn[y];
+                if (!std::isfinite(hn[y])) {
+                    c->err = "batched Krylov solver: non-finite Arnoldi coefficient";
+                    return OVL_EBREAKDOWN;
+                }
+                if (hn[y] > 0) CK(O::axpby(c, 1.0 / hn[y], k.w + (long)y * n, 0.0, vec(k.V, j + 1, y)));
+                else CK(cudaMemsetAsync(vec(k.V, j + 1, y), 0, n * sizeof(T), c->stream));
+                for (int i = 0; i < j; i++) {
+                    const cd a = Hy[(size_t)i * m + j], bq = Hy[(size_t)(i + 1) * m + j];
+                    Hy[(size_t)i * m + j] = std::conj(cs[y][i]) * a + std::conj(sn[y][i]) * bq;
+                    Hy[(size_t)(i + 1) * m + j] = -sn[y][i] * a + cs[y][i] * bq;
+                }
+                const cd a = Hy[(size_t)j * m + j], bq = Hy[(size_t)(j + 1) * m + j];
+                const double den = sqrt(std::norm(a) + std::norm(bq));
+                cs[y][j] = den > 0 ? a / den : cd(1.0);
+                sn[y][j] = den > 0 ? bq / den : cd(0.0);
+                Hy[(size_t)j * m + j] = den;
+                Hy[(size_t)(j + 1) * m + j] = 0.0;
+                gv[y][j + 1] = -sn[y][j] * gv[y][j];
+                gv[y][j] = std::conj(cs[y][j]) * gv[y][j];
+                if (std::abs(gv[y][j + 1]) <= tol * bnorm[y] || hn[y] == 0.0) live[y] = 0;
+            }
+            its++;
+            if (its >= maxit) {
+                j++;
+                break;
+            }
+        }
+        // x_y += Z_y (H_y^{-1} g_y) over the columns this system took
+        for (int y = 0; y < nb; y++) {
+            if (!active[y]) continue;
+            int jy = 0;   // columns used by y: those with nonzero diagonal
+            while (jy < j && std::abs(H[y][(size_t)jy * m + jy]) > 0) jy++;
+            if (!jy) continue;
+            std::vector<cd> yy(jy);
+            for (int i = jy - 1; i >= 0; i--) {
+                cd sacc = gv[y][i];
+                for (int q = i + 1; q < jy; q++) sacc -= H[y][(size_t)i * m + q] * yy[q];
+                yy[i] = sacc / H[y][(size_t)i * m + i];
+            }
+            ST(upload_coef(c, yy));
+            CK(O::multiaxpy(c, vec(k.Z, 0, y), jy, c->d_coef, x + (long)y * n, (long)nb * n));
+            ST(c->sync());
+            rel[y] = std::abs(gv[y][jy]) / bnorm[y];
+            // reset this system's Hessenberg for the next cycle
+            std::fill(H[y].begin(), H[y].end(), cd(0));
+        }
+        xz = false;
+        if (!verify) {
+            bool any_left = false;
+            for (int y = 0; y < nb; y++)
+                if (active[y]) {
+                    if (rel[y] <= tol) {
+                        active[y] = 0;
+                        conv[y] = 1;
+                    } else {
+                        any_left = true;
+                    }
+                }
+            if (!any_left || its >= maxit) break;
+        }
+    }
+    *iters = its;
+    for (int y = 0; y < nb; y++) {
+        rel_out[y] = conv[y] ? std::min(rel[y], tol) : rel[y];
+        conv_out[y] = conv[y];
+    }
+    return OVL_OK;
+}
+
+// SAP-preconditioned batched Wilson solve (precision T), tolerance eps for every system.
+template <typename T>
+ovl_status wilson_solve_batch(Ctx *c, int nb, const T *in, T *out, double m0, double eps, const char *active) {
+    Krylov<T> &k = sizeof(T) == 8 ? (Krylov<T> &)c->kbo_wil64 : (Krylov<T> &)c->kbo_wil32;
+    int &cap = c->kb_n[sizeof(T) == 8 ? 3 : 2];
+    ST(ensure_krylov_batch<T>(c, k, cap, std::min(c->p.prec_restart, 16), nb));
+    T *&scratch = sizeof(T) == 8 ? (T *&)c->sap_r64 : (T *&)c->sap_r32;
+    if (!scratch) {
+        void *buf;
+        ST(c->alloc(&buf, (size_t)c->n64 * sizeof(T)));
+        scratch = (T *)buf;
+    }
+    const SapGeom sg = make_sap_geom(c->g, c->p.sap_block);
+    const long n = c->n64;
+    auto mv = [&](const T *a, T *o, const double *) -> ovl_status {
+        if (sizeof(T) == 8)
+            CK(wilson_batch_f64(c->g, c->U64, (const double2 *)a, (double2 *)o, (long)c->g.V * 12, nb, m0, 0, 1.0,
+                                nullptr, 0.0, c->stream));
+        else
+            CK(wilson_batch_f32(c->g, c->U32, (const float4 *)a, (float4 *)o, (long)c->g.V * 6, nb, (float)m0, 0,
+                                1.f, nullptr, 0.f, c->stream));
+        return OVL_OK;
+    };
+    auto pc = [&](const T *a, T *o, const char *act) -> ovl_status {
+        for (int y = 0; y < nb; y++)
+            if (act[y]) CK(Ops<T>::sap(c, sg, a + (long)y * n, o + (long)y * n, scratch, m0));
+            else CK(cudaMemsetAsync(o + (long)y * n, 0, n * sizeof(T), c->stream));
+        return OVL_OK;
+    };
+    int its;
+    std::vector<double> rel(nb);
+    std::unique_ptr<bool[]> conv(new bool[nb]);
+    (void)active;
+    ST(fgmres_batch<T>(c, k, nb, out, in, eps, c->p.prec_max_iter, true, mv, pc, &its, rel.data(), conv.get(),
+                       false));
+    c->stat_prec += (long)its * nb;
+    return OVL_OK;
+}
+
+}  // namespace
+
+// Bytes of device memory one batched right-hand side needs (Krylov bases, multishift and
+// staging vectors) with the restart lengths the batched solver uses.
+static size_t batch_bytes_per_rhs(const Ctx *c) {
+    const double v64 = (double)c->n64 * 8.0, v32 = (double)c->n64 * 4.0;
+    const int mo = std::min(c->p.restart, 32), mi = std::min(c->p.restart_inner, 32), mw = std::min(c->p.prec_restart, 16);
+    double b = (2 * mo + 3) * v64 + (c->npole + 3) * v64 + 2 * v64;                 // outer + FP64 multishift + x, b
+    b += (2 * mi + 3) * v32 + (2 * mw + 3) * v32 + (c->npole + 3) * v32 + 2 * v32;  // inner, Wilson, FP32 multishift
+    return (size_t)b;
+}
+
+int batch_size_for(Ctx *c, int want) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const size_t per = batch_bytes_per_rhs(c);
+    // keep 10% of the device (at least 8 GB) free for staging and later calls
+    const size_t keep = std::max((size_t)8 << 30, tot / 10);
+    const size_t budget = fr > keep ? fr - keep : 0;
+    int nb = std::min(want, kMaxBatch);
+    while (nb > 1 && per * (size_t)nb > budget) nb--;
+    return nb;
+}
+
+ovl_status solve_batch(Ctx *c, double2 *x, const double2 *b, int nb, double tol, int *outer_iters, double *worst_res,
+                       bool *all_conv) {
+    const long n = c->n64;
+    ST(ensure_krylov_batch<double>(c, c->kbo_outer, c->kb_n[0], std::min(c->p.restart, 32), nb));
+    const bool mixed = c->p.precision != OVL_FP64 || c->p.precond == OVL_PREC_RECURSIVE;
+    // FP32 staging for nb vectors
+    float *fa = nullptr, *fb = nullptr;
+    {
+        static_assert(sizeof(float4) == 16, "");
+        if (!c->fbat || c->fbat_cap < nb) {
+            void *buf;
+            ST(c->alloc(&buf, (size_t)n * sizeof(float) * 2 * nb));
+            c->fbat = (float *)buf;
+            c->fbat_cap = nb;
+        }
+        fa = c->fbat;
+        fb = c->fbat + (long)nb * n;
+    }
+    const double tight = std::max(1e-14, std::min(c->p.sign_tol, 0.1 * tol));
+    const double low_ok = c->p.precision == OVL_MIXED_HALF ? 1e-3 : 1e-5;
+    // inner batched FP32 FGMRES on D_N, preconditioned by the batched Wilson solve
+    auto inner = [&](const float *in, float *out, const char *act) -> ovl_status {
+        ST(ensure_krylov_batch<float>(c, c->kbo_inner, c->kb_n[1], std::min(c->p.restart_inner, 32), nb));
+        const double eps = c->p.eps_inner;
+        auto mv = [&](const float *a, float *o, const double *relv) -> ovl_status {
+            double t[kMaxBatch];
+            for (int y = 0; y < nb; y++)
+                t[y] = relv[y] >= 1.5 ? 0.0 : relax_tol(c, eps, relv[y] < 0 ? eps : relv[y], 1e-6, 1e-1);
+            return c->sign32_batch((const float4 *)a, (float4 *)o, nb, t, 1);
+        };
+        auto pc = [&](const float *a, float *o, const char *act2) -> ovl_status {
+            CK(zero_inactive<float>(c, const_cast<float *>(a), nb, act2));
+            return wilson_solve_batch<float>(c, nb, a, o, c->m0_prec, c->p.eps_prec, act2);
+        };
+        int its;
+        std::vector<double> rel(nb);
+        std::unique_ptr<bool[]> conv(new bool[nb]);
+        (void)act;
+        ST(fgmres_batch<float>(c, c->kbo_inner, nb, out, in, eps, c->p.max_inner, true, mv, pc, &its, rel.data(),
+                               conv.get(), false));
+        c->stat_inner += its * nb;
+        return OVL_OK;
+    };
+    auto mv = [&](const double *a, double *o, const double *relv) -> ovl_status {
+        double t[kMaxBatch];
+        bool low = mixed;
+        for (int y = 0; y < nb; y++) {
+            if (relv[y] >= 1.5) t[y] = 0.0;   // converged system: no work
+            else t[y] = relv[y] < 0 ? tight : relax_tol(c, tol, relv[y], tight, 1e-1);
+            if (t[y] > 0 && (relv[y] < 0 || t[y] < low_ok)) low = false;
+        }
+        if (low) {
+            CK(spinor_d2f_n(c, (const double2 *)a, (float4 *)fa, nb));
+            ST(c->sign32_batch((const float4 *)fa, (float4 *)fb, nb, t, 1));
+            CK(spinor_f2d_n(c, (const float4 *)fb, (double2 *)o, nb));
+            return OVL_OK;
+        }
+        return c->sign64_batch((const double2 *)a, (double2 *)o, nb, t, 1);
+    };
+    auto pc = [&](const double *a, double *o, const char *act) -> ovl_status {
+        if (!mixed && c->p.precond == OVL_PREC_WILSON) {
+            CK(zero_inactive<double>(c, const_cast<double *>(a), nb, act));
+            return wilson_solve_batch<double>(c, nb, a, o, c->m0_prec, c->p.eps_prec, act);
+        }
+        if (c->p.precond == OVL_PREC_NONE) {
+            CK(cudaMemcpyAsync(o, a, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            return OVL_OK;
+        }
+        CK(spinor_d2f_n(c, (const double2 *)a, (float4 *)fa, nb));
+        CK(zero_inactive<float>(c, fa, nb, act));
+        if (c->p.precond == OVL_PREC_WILSON) ST(wilson_solve_batch<float>(c, nb, fa, fb, c->m0_prec, c->p.eps_prec, act));
+        else ST(inner(fa, fb, act));
+        CK(spinor_f2d_n(c, (const float4 *)fb, (double2 *)o, nb));
+        return OVL_OK;
+    };
+    // x holds the initial guesses; start from zero when all of them are zero
+    double nx = 0.0;
+    for (int y = 0; y < nb; y++) {
+        double v;
+        ST(c->norm2_d((const double *)(x + (long)y * (n / 2)), &v));
+        nx += v;
+    }
+    int its;
+    std::vector<double> rel(nb);
+    std::unique_ptr<bool[]> conv(new bool[nb]);
+    ST(fgmres_batch<double>(c, c->kbo_outer, nb, (double *)x, (const double *)b, tol, c->p.max_iter, nx == 0.0, mv,
+                            pc, &its, rel.data(), conv.get(), true));
+    *outer_iters = its * nb;
+    *worst_res = 0.0;
+    *all_conv = true;
+    for (int y = 0; y < nb; y++) {
+        *worst_res = std::max(*worst_res, rel[y]);
+        *all_conv = *all_conv && conv[y];
     }
     return OVL_OK;
 }

@@ -12,9 +12,11 @@ struct GraphSlot {
     cudaGraphExec_t exec = nullptr;
     int chunk = 0;
     bool prof = false;
+    int nrhs = 0;
 };
 
 constexpr int kMaxChunk = 64;
+constexpr int kScal = 8192;   // doubles of scalar staging (device d_scal, pinned h_scal)
 
 // Event timings of the multishift kernels (instrumentation).
 struct ProfAcc {
@@ -45,7 +47,7 @@ struct Ctx {
     std::vector<void *> allocs;
     size_t bytes_held = 0;
     void *h_pinned = nullptr;
-    double *h_scal = nullptr;     // pinned scalars (512 doubles)
+    double *h_scal = nullptr;     // pinned scalars (kScal doubles; coefficient staging in the upper half)
     int *h_flag = nullptr;
     int *h_ms_small = nullptr;
     MsState *h_ms = nullptr;
@@ -71,7 +73,17 @@ struct Ctx {
     MsVectors<float4> ms32{};
     MsVectorsH msh{};
     MsState *msh_state = nullptr;
-    GraphSlot graphs[4];
+    GraphSlot graphs[6];
+    // batched multishift (several right-hand sides in lock-step)
+    MsBatch<double2> msb64{};
+    MsBatch<float4> msb32{};
+    int msb64_cap = 0, msb32_cap = 0;
+    MsState *msb_state = nullptr;      // kMaxBatch states
+    MsState *h_msb = nullptr;          // pinned host copies
+    int *h_msb_small = nullptr;        // pinned: 4 ints per state
+    RedScratch rsb{};                  // per-row partials for batched reductions
+    unsigned *bcounters = nullptr;     // per-row arrival counters
+    void *h_pinned_b = nullptr;
     // instrumentation
     bool prof = false;
     ProfAcc pacc[2];   // per precision slot (0 FP64, 1 FP32)
@@ -84,6 +96,13 @@ struct Ctx {
     // Krylov workspaces
     Krylov<double> kry_outer, kry_wil64;
     Krylov<float> kry_inner, kry_wil32;
+    Krylov<double> kbo_outer, kbo_wil64;   // batched: N vectors per basis entry
+    Krylov<float> kbo_inner, kbo_wil32;
+    int kb_n[4] = {0, 0, 0, 0};
+    float *fbat = nullptr;             // FP32 staging of a batch (2 x nb vectors)
+    int fbat_cap = 0;
+    double2 *xbat = nullptr, *bbat = nullptr;   // FP64 batch of solutions / right-hand sides
+    int xbat_cap = 0;
     float *f_a = nullptr, *f_b = nullptr;   // FP32 conversion buffers
     void *sap_r32 = nullptr, *sap_r64 = nullptr;   // SAP residual scratch
     double2 *d_x = nullptr, *d_b = nullptr; // FP64 solve vectors
@@ -110,6 +129,12 @@ struct Ctx {
     ovl_status ensure_ms64();
     ovl_status ensure_ms32();
     ovl_status ensure_msh();
+    // several right-hand sides: b, out hold nrhs internal vectors back to back
+    ovl_status ensure_batch();
+    ovl_status sign64_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode);
+    ovl_status sign32_batch(const float4 *b, float4 *out, int nrhs, const double *tol, int mode);
+    template <typename ST, typename Init, typename Iter>
+    ovl_status msb_run(int nrhs, const double *tol, int slot, Init init_fn, Iter iter_fn, long *iters_out);
     ovl_status lanczos_bounds(double *lmin, double *lmax);
     ovl_status sigma_min_estimate(double *smin);
     ovl_status set_zolotarev();
@@ -117,6 +142,9 @@ struct Ctx {
 };
 
 ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats);
+// Lock-step batched solve of nrhs <= kMaxBatch systems on internal FP64 vectors.
+ovl_status solve_batch(Ctx *c, double2 *x, const double2 *b, int nrhs, double tol, int *outer_iters,
+                       double *worst_res, bool *all_conv);
 // Inexact Wilson solve on FP64 even-odd spinors (FP32 inside unless precision == FP64).
 ovl_status wilson_solve_eo(Ctx *c, const double2 *b, double2 *x, double m0, double tol, int *iters);
 

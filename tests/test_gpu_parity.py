@@ -273,7 +273,7 @@ def test_config4_half_storage_full_size():
     FP64 outer FGMRES, tol 1e-10. The oracle cannot solve at this size; the check is the
     true residual through the FP64 D_N (itself pinned to the oracle at smaller volumes)."""
     dims = (64, 32, 32, 32)
-    U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1004, stout_steps=3)).cuda()
+    U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1004, stout_steps=3, device="cuda")).cuda()
     b = torch.from_numpy(synth.rhs_z2(dims, 2004)).cuda()
     op = ovl.Overlap(U, dims, 1.0, 0.01, ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE,
                                                             precision=ovl.OVL_MIXED_HALF))
@@ -285,3 +285,11 @@ def test_config4_half_storage_full_size():
     assert res < 2e-10, (res, stats)
     assert stats["ms_iters_low"] > 0
     op.close()
+
+
+def test_gauge_generator_torch_path_matches_numpy():
+    """The device path of the input generator reproduces the numpy path to rounding."""
+    dims = (4, 4, 4, 6)
+    a = synth.gauge_field(dims, 0.5, 77, stout_steps=2)
+    b = synth.gauge_field(dims, 0.5, 77, stout_steps=2, device="cuda")
+    assert np.abs(a - b).max() < 1e-12
