@@ -234,6 +234,59 @@ ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset);
 ovl_status wilson_apply_noalloc(double *out, const double *in, const double *gauge, const int dims[4],
                                 double m0, int antiperiodic, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------------
+ * Serving: overlap solves submitted as they arrive, run concurrently on the current GPU.
+ * (Not part of the paper's method; a service layer around ovl_create/ovl_solve.)
+ * `slots` worker threads run requests concurrently; every context issues its work on a CUDA
+ * stream of its own, so the kernels of concurrent requests overlap on the device. A queued request starts as soon as a slot is
+ * free and its estimated device memory fits hbm_budget next to the running requests and
+ * the cached contexts (first fit in arrival order). After a request completes its context
+ * (gauge field, spectral interval, coefficients, workspaces) stays resident, keyed by
+ * gauge_key and the operator parameters, and later requests with the same key reuse it;
+ * idle contexts are evicted least recently used first when memory is needed.
+ * --------------------------------------------------------------------------------- */
+typedef struct ovl_server ovl_server;
+
+typedef struct {
+    const double *gauge;        /* V*4*9 complex doubles (host or device), as for ovl_create */
+    long gauge_key;             /* nonzero: reuse resident contexts of equal key and operator */
+    int dims[4];
+    double rho, mu;
+    int n_rhs;
+    const double *b;            /* n_rhs right-hand sides (host or device) */
+    double *x;                  /* n_rhs initial guesses in, solutions out */
+    double tol;                 /* 0 = params.tol_outer */
+    const ovl_params *params;   /* NULL = defaults; copied at submission */
+} ovl_request;
+
+typedef struct {
+    int done;                   /* 1 once finished (successfully or not) */
+    ovl_status status;
+    ovl_stats stats;
+    double queue_s;             /* submission -> start */
+    double run_s;               /* start -> completion */
+    double latency_s;           /* submission -> completion */
+    size_t device_bytes;        /* device memory the request held */
+    char message[160];          /* error text when status != OVL_OK */
+} ovl_result;
+
+/* slots: concurrent requests (1..64); hbm_budget: bytes of device memory the server may use
+ * (0 = 90% of the free memory at creation). */
+ovl_status ovl_server_create(ovl_server **srv, int slots, size_t hbm_budget);
+/* Queues a request and returns its ticket. The buffers it points to (gauge, b, x) must stay
+ * valid until the request is done. OVL_ENOMEM: the request can never fit the budget. */
+ovl_status ovl_server_submit(ovl_server *srv, const ovl_request *req, long *ticket);
+/* Non-blocking status of a ticket (res->done == 0 while queued or running). */
+ovl_status ovl_server_query(ovl_server *srv, long ticket, ovl_result *res);
+/* Blocks until the ticket's request is done; res may be NULL. */
+ovl_status ovl_server_wait(ovl_server *srv, long ticket, ovl_result *res);
+/* Latency percentiles (s) over completed requests, completed requests per second of wall time
+ * (first submission to last completion), reserved-memory high-water mark. Nullable outputs. */
+ovl_status ovl_server_report(ovl_server *srv, double *p50, double *p99, double *solves_per_s,
+                             size_t *hbm_high_water, long *completed, long *failed);
+/* Finishes the queued requests, stops the workers and frees every resident context. */
+ovl_status ovl_server_destroy(ovl_server *srv);
+
 /* Destroys the context and frees its device memory. NULL is a no-op. */
 ovl_status ovl_destroy(ovl_ctx *ctx);
 

@@ -54,6 +54,24 @@ class ovl_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ovl_request(ctypes.Structure):
+    _fields_ = [("gauge", ctypes.c_void_p), ("gauge_key", ctypes.c_long), ("dims", ctypes.c_int * 4),
+                ("rho", ctypes.c_double), ("mu", ctypes.c_double), ("n_rhs", ctypes.c_int),
+                ("b", ctypes.c_void_p), ("x", ctypes.c_void_p), ("tol", ctypes.c_double),
+                ("params", ctypes.c_void_p)]
+
+
+class ovl_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("stats", ovl_stats),
+                ("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("message", ctypes.c_char * 160)]
+
+    def as_dict(self):
+        return {"done": self.done, "status": self.status, "stats": self.stats.as_dict(), "queue_s": self.queue_s,
+                "run_s": self.run_s, "latency_s": self.latency_s, "device_bytes": self.device_bytes,
+                "message": self.message.decode(errors="replace")}
+
+
 class ovl_prof_kernel(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_long), ("bytes", ctypes.c_double),
                 ("flops", ctypes.c_double)]
@@ -75,7 +93,8 @@ class ovl_prof(ctypes.Structure):
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
            "wilson_solve", "ovl_tuning", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
-           "ovl_apply_n", "ovl_dslash_time_n"]
+           "ovl_apply_n", "ovl_dslash_time_n", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
+           "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
 _lib = None
 
@@ -108,6 +127,14 @@ def lib():
         L.wilson_apply_n.argtypes = [P, P, P, I_, D]
         L.ovl_apply_n.argtypes = [P, P, P, I_, D]
         L.ovl_dslash_time_n.argtypes = [P, I_, I_, I_, ctypes.POINTER(D)]
+        L.ovl_server_create.argtypes = [ctypes.POINTER(P), I_, ctypes.c_size_t]
+        L.ovl_server_submit.argtypes = [P, ctypes.POINTER(ovl_request), ctypes.POINTER(ctypes.c_long)]
+        L.ovl_server_query.argtypes = [P, ctypes.c_long, ctypes.POINTER(ovl_result)]
+        L.ovl_server_wait.argtypes = [P, ctypes.c_long, ctypes.POINTER(ovl_result)]
+        L.ovl_server_report.argtypes = [P] + [ctypes.POINTER(D)] * 3 + [ctypes.POINTER(ctypes.c_size_t),
+                                                                         ctypes.POINTER(ctypes.c_long),
+                                                                         ctypes.POINTER(ctypes.c_long)]
+        L.ovl_server_destroy.argtypes = [P]
         for name in EXPORTS:
             if name not in ("ovl_last_error",):
                 getattr(L, name).restype = I_
@@ -321,3 +348,61 @@ class Overlap:
 
     def prof_get(self, reset=False):
         return ovl_prof_get(self.ctx, reset)
+
+
+class Server:
+    """The library's serving loop (ovl_server_*): submit overlap solves as they arrive.
+
+    Buffers passed to submit() must stay alive until the request is done; the object
+    keeps references to them for that reason."""
+
+    def __init__(self, slots=2, hbm_budget=0):
+        self.h = ctypes.c_void_p()
+        _check(lib().ovl_server_create(ctypes.byref(self.h), int(slots), int(hbm_budget)))
+        self._keep = {}
+
+    def submit(self, gauge, dims, rho, mu, b, x, n_rhs=1, tol=0.0, params=None, gauge_key=0):
+        req = ovl_request()
+        req.gauge = _ptr(gauge).value
+        req.gauge_key = int(gauge_key)
+        for m in range(4):
+            req.dims[m] = int(dims[m])
+        req.rho, req.mu, req.n_rhs, req.tol = float(rho), float(mu), int(n_rhs), float(tol)
+        req.b = _ptr(b).value
+        req.x = _ptr(x, True).value
+        req.params = ctypes.cast(ctypes.byref(params), ctypes.c_void_p).value if params is not None else None
+        t = ctypes.c_long()
+        _check(lib().ovl_server_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = (gauge, b, x, params)
+        return t.value
+
+    def query(self, ticket):
+        r = ovl_result()
+        _check(lib().ovl_server_query(self.h, ctypes.c_long(ticket), ctypes.byref(r)))
+        return r.as_dict()
+
+    def wait(self, ticket):
+        r = ovl_result()
+        _check(lib().ovl_server_wait(self.h, ctypes.c_long(ticket), ctypes.byref(r)))
+        self._keep.pop(ticket, None)
+        return r.as_dict()
+
+    def report(self):
+        p50, p99, sps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        hw, done, failed = ctypes.c_size_t(), ctypes.c_long(), ctypes.c_long()
+        _check(lib().ovl_server_report(self.h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(sps),
+                                       ctypes.byref(hw), ctypes.byref(done), ctypes.byref(failed)))
+        return {"p50_s": p50.value, "p99_s": p99.value, "solves_per_s": sps.value, "hbm_high_water": hw.value,
+                "completed": done.value, "failed": failed.value}
+
+    def close(self):
+        if self.h:
+            _check(lib().ovl_server_destroy(self.h))
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
