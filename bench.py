@@ -276,8 +276,82 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": prof["launches"],
         "clocks": clocks,
     }
+    out["dslash"] = dslash(ovl, torch, dev, pk["hbm_gbs"])
+    out["serving"] = serving(ovl, torch, dev)
     out["cpu_baseline"] = cpu_baseline(st_64[-1], budget_s=args.cpu_budget)
     return out
+
+
+def dslash(ovl, torch, dev, hbm_gbs, dims=(64, 32, 32, 32)):
+    """Wilson stencil alone at 32^3 x 64 (working set larger than L2): 96 algorithmic reals
+    per site (each link and spinor once); multi-RHS: 48/n link reals + 48 spinor reals per
+    site and right-hand side."""
+    import numpy as np
+    import synth
+    V = int(np.prod(dims))
+    U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1004, stout_steps=0, device=dev)).to(dev)
+    op = ovl.Overlap(U, dims, 1.0, 0.01, ovl.params_default(lambda_min=0.3, lambda_max=7.3))
+    out = {"lattice": "x".join(map(str, dims)), "byte_model": "96 reals/site (48 link + 24 in + 24 out)"}
+    for prec, name, w in ((1, "fp32", 4), (0, "fp64", 8)):
+        ms = op.dslash_time(prec, 20)
+        gbs = 96 * V * w / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "GB/s": gbs, "frac_hbm": gbs / hbm_gbs, "GFLOP/s": 1368 * V / (ms * 1e-3) / 1e9}
+    for nr in (4, 12):
+        ms = op.dslash_time_n(1, nr, 10)
+        gbs = (48.0 / nr + 48.0) * nr * V * 4 / (ms * 1e-3) / 1e9
+        out["fp32_rhs%d" % nr] = {"ms": ms, "ms_per_rhs": ms / nr, "GB/s": gbs, "frac_hbm": gbs / hbm_gbs}
+    op.close()
+    return out
+
+
+def serving(ovl, torch, dev, n_req=24, slots=3, seed=5000):
+    """Config-5 sample: overlap solves of 8^4 and 16^4 lattices (3-stout links, 6 gauge
+    configurations shared among the requests), mu in {0.01, 0.05, 0.1}, 1-4 Gaussian
+    right-hand sides, tol 1e-8. Capacity is measured with all requests submitted at once;
+    then the same requests arrive as a Poisson stream at 0.7 x capacity."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(seed)
+    lat = [(8, 8, 8, 8), (16, 16, 16, 16)]
+    gauges = {}
+    reqs = []
+    for k in range(n_req):
+        d = lat[int(rng.integers(2))]
+        g = int(k % 6)
+        if (d, g) not in gauges:
+            gauges[(d, g)] = synth.gauge_field(d, 0.5, seed + g, stout_steps=3, device=dev)
+        nr = int(rng.integers(1, 5))
+        reqs.append(dict(dims=d, key=1 + g + 100 * lat.index(d), gauge=gauges[(d, g)],
+                         mu=float(rng.choice([0.01, 0.05, 0.1])), n_rhs=nr,
+                         b=synth.rhs_gaussian(d, seed + 1000 + k, n_rhs=nr)))
+    p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, rhs_block=4)
+
+    def run(arrival_rate):
+        srv = ovl.Server(slots=slots)
+        xs, tk = [], []
+        r2 = np.random.default_rng(seed + 1)
+        for r in reqs:
+            x = np.zeros_like(r["b"])
+            xs.append(x)
+            tk.append(srv.submit(r["gauge"], r["dims"], 1.0, r["mu"], r["b"], x, r["n_rhs"], TOL, p,
+                                 gauge_key=r["key"]))
+            if arrival_rate:
+                time.sleep(float(r2.exponential(1.0 / arrival_rate)))
+        res = [srv.wait(t) for t in tk]
+        rep = srv.report()
+        srv.close()
+        rep["failed_status"] = [x["status"] for x in res if x["status"] != 0]
+        return rep
+
+    run(0.0)                      # warm-up: tuning, graph capture
+    cap = run(0.0)
+    rate = 0.7 * cap["solves_per_s"]
+    st = run(rate)
+    return {"workload": "Poisson stream of %d overlap solves: 8^4/16^4, 3-stout links (6 configurations), "
+                        "mu in {0.01,0.05,0.1}, 1-4 Gaussian RHS, tol 1e-8, %d slots" % (n_req, slots),
+            "arrival_rate_per_s": rate, "capacity_solves_per_s": cap["solves_per_s"],
+            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "solves_per_s": st["solves_per_s"],
+            "completed": st["completed"], "failed": st["failed"], "hbm_high_water_bytes": st["hbm_high_water"]}
 
 
 def cpu_baseline(st64=None, budget_s=15.0):

@@ -75,7 +75,7 @@ __device__ __forceinline__ void block_apply(const R *s, const R *u, int nb, int 
             proj_fwd(mu, v, h0, h1);
             su3_mul(m, h0, a0);
             su3_mul(m, h1, a1);
-            acc_fwd(mu, acc, a0, a1);
+            acc_fwd<false>(mu, acc, a0, a1);
         }
         if (l[mu] > 0) {
             cpx<R> v[12], h0[3], h1[3], a0[3], a1[3], m[3][3];

@@ -11,21 +11,73 @@
 // colour vectors by the link, and rebuilds the lower two spins with a few sign/i
 // swaps: 2 SU(3) x vector products per hop instead of 4.
 //
-// Antiperiodic time boundary: hops across the x0 boundary carry a factor -1.
+// Antiperiodic time boundary: hops across the x0 boundary carry a factor -1, applied as
+// a sign-bit flip of the projected half spinor.
 #pragma once
 #include "common.cuh"
 
 namespace ovl {
 
 template <typename R>
+__device__ __forceinline__ R fma_r(R a, R b, R c);
+template <>
+__device__ __forceinline__ double fma_r<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_r<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// o = u h and o = u^H h as explicit chains of fused multiply-adds: per output real one
+// multiply and five FMAs. Summing separately rounded complex products would cost two
+// more instructions per output real (the compiler does not reassociate), about a fifth
+// of the FP64 stencil's FP64 instructions.
+template <typename R>
 __device__ __forceinline__ void su3_mul(const cpx<R> u[3][3], const cpx<R> h[3], cpx<R> o[3]) {
 #pragma unroll
-    for (int a = 0; a < 3; a++) o[a] = u[a][0] * h[0] + u[a][1] * h[1] + u[a][2] * h[2];
+    for (int a = 0; a < 3; a++) {
+        R re = u[a][0].re * h[0].re, im = u[a][0].re * h[0].im;
+        re = fma_r(-u[a][0].im, h[0].im, re);
+        im = fma_r(u[a][0].im, h[0].re, im);
+#pragma unroll
+        for (int b = 1; b < 3; b++) {
+            re = fma_r(u[a][b].re, h[b].re, re);
+            im = fma_r(u[a][b].re, h[b].im, im);
+            re = fma_r(-u[a][b].im, h[b].im, re);
+            im = fma_r(u[a][b].im, h[b].re, im);
+        }
+        o[a] = cpx<R>{re, im};
+    }
 }
 template <typename R>
 __device__ __forceinline__ void su3_dag_mul(const cpx<R> u[3][3], const cpx<R> h[3], cpx<R> o[3]) {
 #pragma unroll
-    for (int a = 0; a < 3; a++) o[a] = cmul_conj(u[0][a], h[0]) + cmul_conj(u[1][a], h[1]) + cmul_conj(u[2][a], h[2]);
+    for (int a = 0; a < 3; a++) {
+        R re = u[0][a].re * h[0].re, im = u[0][a].re * h[0].im;
+        re = fma_r(u[0][a].im, h[0].im, re);
+        im = fma_r(-u[0][a].im, h[0].re, im);
+#pragma unroll
+        for (int b = 1; b < 3; b++) {
+            re = fma_r(u[b][a].re, h[b].re, re);
+            im = fma_r(u[b][a].re, h[b].im, im);
+            re = fma_r(u[b][a].im, h[b].im, re);
+            im = fma_r(-u[b][a].im, h[b].re, im);
+        }
+        o[a] = cpx<R>{re, im};
+    }
+}
+
+// -x where neg != 0, by flipping the sign bit (integer pipe, exact)
+__device__ __forceinline__ double flip_sign(double x, bool neg) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+}
+__device__ __forceinline__ float flip_sign(float x, bool neg) {
+    return __int_as_float(__float_as_int(x) ^ (neg ? (int)0x80000000u : 0));
+}
+template <typename R>
+__device__ __forceinline__ void flip_half(cpx<R> h0[3], cpx<R> h1[3], bool neg) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        h0[c] = cpx<R>{flip_sign(h0[c].re, neg), flip_sign(h0[c].im, neg)};
+        h1[c] = cpx<R>{flip_sign(h1[c].re, neg), flip_sign(h1[c].im, neg)};
+    }
 }
 
 // Forward hop, spin part (1 - gamma_mu): project psi(x+mu) to h0, h1.
@@ -42,18 +94,28 @@ __device__ __forceinline__ void proj_fwd(int mu, const cpx<R> s[12], cpx<R> h0[3
         }
     }
 }
-// Forward hop: add [a0; a1; -A^H (a0, a1)] into acc.
-template <typename R>
+// Forward hop: add [a0; a1; -A^H (a0, a1)] into acc (First: acc is empty, assign).
+template <bool First, typename R>
 __device__ __forceinline__ void acc_fwd(int mu, cpx<R> acc[12], const cpx<R> a0[3], const cpx<R> a1[3]) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        acc[c] = acc[c] + a0[c];
-        acc[3 + c] = acc[3 + c] + a1[c];
+        cpx<R> l2, l3;   // lower two spins of the contribution
         switch (mu) {
-            case 0: acc[6 + c] = acc[6 + c] - a0[c];        acc[9 + c] = acc[9 + c] - a1[c];        break;
-            case 1: acc[6 + c] = acc[6 + c] + mul_mi(a1[c]); acc[9 + c] = acc[9 + c] + mul_mi(a0[c]); break;
-            case 2: acc[6 + c] = acc[6 + c] - a1[c];        acc[9 + c] = acc[9 + c] + a0[c];        break;
-            default: acc[6 + c] = acc[6 + c] + mul_mi(a0[c]); acc[9 + c] = acc[9 + c] + mul_i(a1[c]); break;
+            case 0: l2 = -a0[c];        l3 = -a1[c];        break;
+            case 1: l2 = mul_mi(a1[c]); l3 = mul_mi(a0[c]); break;
+            case 2: l2 = -a1[c];        l3 = a0[c];         break;
+            default: l2 = mul_mi(a0[c]); l3 = mul_i(a1[c]); break;
+        }
+        if (First) {
+            acc[c] = a0[c];
+            acc[3 + c] = a1[c];
+            acc[6 + c] = l2;
+            acc[9 + c] = l3;
+        } else {
+            acc[c] = acc[c] + a0[c];
+            acc[3 + c] = acc[3 + c] + a1[c];
+            acc[6 + c] = acc[6 + c] + l2;
+            acc[9 + c] = acc[9 + c] + l3;
         }
     }
 }
@@ -96,8 +158,6 @@ __device__ __forceinline__ void wilson_hop(const Geom &g, const LT *__restrict__
     eo_coords(g, p, i, x);
     const int q = 1 - p;
 #pragma unroll
-    for (int c = 0; c < 12; c++) acc[c] = cpx<R>{0, 0};
-#pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         {   // forward neighbour x + mu, link U_mu(x) stored at (p, i)
             int y[4] = {x[0], x[1], x[2], x[3]};
@@ -107,13 +167,11 @@ __device__ __forceinline__ void wilson_hop(const Geom &g, const LT *__restrict__
             load_spinor<R>(in, g.Vh, q, j, s);
             load_link<R>(U, g.Vh, p, mu, i, u);
             proj_fwd(mu, s, h0, h1);
+            if (mu == 0) flip_half(h0, h1, g.antiperiodic && x[0] == g.L[0] - 1);
             su3_mul(u, h0, a0);
             su3_mul(u, h1, a1);
-            if (mu == 0 && g.antiperiodic && x[0] == g.L[0] - 1) {
-#pragma unroll
-                for (int c = 0; c < 3; c++) { a0[c] = -a0[c]; a1[c] = -a1[c]; }
-            }
-            acc_fwd(mu, acc, a0, a1);
+            if (mu == 0) acc_fwd<true>(mu, acc, a0, a1);
+            else acc_fwd<false>(mu, acc, a0, a1);
         }
         {   // backward neighbour x - mu, link U_mu(x - mu)^H stored at (q, j)
             int y[4] = {x[0], x[1], x[2], x[3]};
@@ -123,12 +181,9 @@ __device__ __forceinline__ void wilson_hop(const Geom &g, const LT *__restrict__
             load_spinor<R>(in, g.Vh, q, j, s);
             load_link<R>(U, g.Vh, q, mu, j, u);
             proj_bwd(mu, s, h0, h1);
+            if (mu == 0) flip_half(h0, h1, g.antiperiodic && x[0] == 0);
             su3_dag_mul(u, h0, a0);
             su3_dag_mul(u, h1, a1);
-            if (mu == 0 && g.antiperiodic && x[0] == 0) {
-#pragma unroll
-                for (int c = 0; c < 3; c++) { a0[c] = -a0[c]; a1[c] = -a1[c]; }
-            }
             acc_bwd(mu, acc, a0, a1);
         }
     }
