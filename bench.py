@@ -187,6 +187,7 @@ def run_ours(args, rank, world, dist):
     op = ovl.Overlap(torch.from_numpy(U).to(dev), DIMS, 1.0, 0.01, solver_params(ovl, True),
                      stream=stream.cuda_stream)
     info = op.info()
+    tuning, tuning_sap = op.tuning(), op.tuning_sap()
     with Clocks(dev_idx) as clk:
         ms_mixed, st_mixed, prof = timed_solves(op, args.steps, args.warmup, prof=True)
     clocks = clk.summary()
@@ -260,6 +261,10 @@ def run_ours(args, rank, world, dist):
         "mixed_stats": st_mixed[-1],
         "true_rel_resid": res_true,
         "spectral": info,
+        "tuning": {"stencil_tps_fp64": tuning["tps64"], "stencil_tps_fp32": tuning["tps32"],
+                   "stencil_ms_fp64_tps1_tps4_fp32_tps1_tps4": [round(v, 4) for v in tuning["ms"]],
+                   "sap_tps": tuning_sap["sap_tps"],
+                   "sap_cycle_ms_tps1_2_4": [round(v, 4) for v in tuning_sap["ms"]]},
         "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": (achieved / peak) if achieved else None, "peak_kind": pkind,
                      "traffic": traffic_from_profiles(dom), "algorithmic_bytes_per_launch": per_launch_bytes,

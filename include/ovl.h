@@ -59,7 +59,8 @@ typedef enum {
 typedef enum {
     OVL_FP64 = 0,         /* everything in FP64 */
     OVL_MIXED_FP32 = 1,   /* inner (preconditioner) work in FP32, outer D_N in FP64 */
-    OVL_MIXED_HALF = 2    /* as MIXED_FP32, inner multishift vectors stored in FP16 */
+    OVL_MIXED_HALF = 2,   /* as MIXED_FP32, inner multishift vectors stored in FP16 */
+    OVL_MIXED_BF16 = 3    /* as MIXED_FP32, inner multishift vectors stored in BF16 */
 } ovl_precision;
 
 typedef enum {
@@ -99,6 +100,7 @@ typedef struct {
     int use_graphs;         /* 1: capture multishift iterations in CUDA graphs */
     int check_every;        /* multishift iterations between host convergence checks */
     int stencil_tps;        /* threads per lattice site of the stencils: 0 = autotune, 1 or 4 = forced */
+    int sap_tps;            /* threads per block site of the FP32 Schwarz block solves: 0 = autotune, 1, 2 or 4 */
 } ovl_params;
 
 /* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
@@ -143,6 +145,12 @@ ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, double m0, dou
  * and the measured ms per full-lattice stencil application of each variant
  * (ms[0..3] = FP64 x1, FP64 x4, FP32 x1, FP32 x4; zeros when forced). Nullable outputs. */
 ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, float *ms);
+
+/* Threads per block site chosen for the FP32 Schwarz block solves of the Wilson
+ * preconditioner (Sec. 5.1 smoother; an implementation choice, the paper has no
+ * counterpart) and the measured time of one Schwarz cycle per variant (ms[3]: 1, 2, 4
+ * threads per site; zeros when not tuned). tps, ms nullable. */
+ovl_status ovl_tuning_sap(const ovl_ctx *ctx, int *tps, float *ms);
 
 /* out_k = D_W(m0) in_k for k < n_rhs (n_rhs vectors back to back), with the multi-RHS
  * stencil: blocks of up to 12 right-hand sides per launch share every link load. */

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libovl.so")
 
 OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ENOCONV, OVL_EBREAKDOWN, OVL_ETIMEOUT, OVL_ECUDA = range(7)
-OVL_FP64, OVL_MIXED_FP32, OVL_MIXED_HALF = range(3)
+OVL_FP64, OVL_MIXED_FP32, OVL_MIXED_HALF, OVL_MIXED_BF16 = range(4)
 OVL_PREC_NONE, OVL_PREC_WILSON, OVL_PREC_RECURSIVE = range(3)
 _STATUS = {0: "OVL_OK", 1: "OVL_EINVAL", 2: "OVL_ENOMEM", 3: "OVL_ENOCONV", 4: "OVL_EBREAKDOWN",
            5: "OVL_ETIMEOUT", 6: "OVL_ECUDA"}
@@ -40,6 +40,7 @@ class ovl_params(ctypes.Structure):
         ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_iters", ctypes.c_int),
         ("prec_restart", ctypes.c_int), ("prec_max_iter", ctypes.c_int), ("rhs_block", ctypes.c_int),
         ("use_graphs", ctypes.c_int), ("check_every", ctypes.c_int), ("stencil_tps", ctypes.c_int),
+        ("sap_tps", ctypes.c_int),
     ]
 
 
@@ -92,7 +93,7 @@ class ovl_prof(ctypes.Structure):
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
-           "wilson_solve", "ovl_tuning", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
+           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
            "ovl_apply_n", "ovl_dslash_time_n", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
@@ -122,6 +123,7 @@ def lib():
         L.ovl_prof_get.argtypes = [P, ctypes.POINTER(ovl_prof), I_]
         L.wilson_solve.argtypes = [P, P, P, D, D, ctypes.POINTER(I_)]
         L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
+        L.ovl_tuning_sap.argtypes = [P, ctypes.POINTER(I_), P]
         L.wilson_apply_noalloc.argtypes = [P, P, P, P, D, I_, P]
         L.ovl_dslash_time.argtypes = [P, I_, I_, ctypes.POINTER(D)]
         L.wilson_apply_n.argtypes = [P, P, P, I_, D]
@@ -251,6 +253,14 @@ def ovl_tuning(ctx):
     return {"tps64": a.value, "tps32": b.value, "ms": ms.tolist()}
 
 
+def ovl_tuning_sap(ctx):
+    import numpy as np
+    a = ctypes.c_int()
+    ms = np.zeros(3, dtype=np.float32)
+    _check(lib().ovl_tuning_sap(ctx, ctypes.byref(a), _ptr(ms)), ctx)
+    return {"sap_tps": a.value, "ms": ms.tolist()}
+
+
 def ovl_dslash_time(ctx, precision, reps=20):
     """Average ms of one full-lattice Wilson stencil launch (precision 0 = FP64, 1 = FP32)."""
     ms = ctypes.c_double()
@@ -330,6 +340,9 @@ class Overlap:
 
     def tuning(self):
         return ovl_tuning(self.ctx)
+
+    def tuning_sap(self):
+        return ovl_tuning_sap(self.ctx)
 
     def dslash_time(self, precision, reps=20):
         return ovl_dslash_time(self.ctx, precision, reps)

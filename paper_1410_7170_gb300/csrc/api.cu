@@ -19,6 +19,7 @@
 
 #include "../../include/ovl.h"
 #include "internal.h"
+#include "sap.h"
 #include "solver.h"
 
 using namespace ovl;
@@ -58,6 +59,7 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->use_graphs = 1;
     p->check_every = 8;
     p->stencil_tps = 0;
+    p->sap_tps = 0;
     return OVL_OK;
 }
 
@@ -77,10 +79,11 @@ static ovl_status validate_params(const ovl_params &p, const int L[4], std::stri
         return OVL_EINVAL;
     }
     if (p.precond < 0 || p.precond > 2) { err = "precond must be 0, 1 or 2"; return OVL_EINVAL; }
-    if (p.precision < 0 || p.precision > 2) { err = "precision must be 0, 1 or 2"; return OVL_EINVAL; }
+    if (p.precision < 0 || p.precision > 3) { err = "precision must be 0, 1, 2 or 3"; return OVL_EINVAL; }
     if (p.max_iter < 1 || p.max_ms_iter < 1 || p.check_every < 1) { err = "iteration caps must be >= 1"; return OVL_EINVAL; }
     if (p.rhs_block < 1 || p.rhs_block > 12) { err = "rhs_block must be in [1,12]"; return OVL_EINVAL; }
     if (p.stencil_tps != 0 && p.stencil_tps != 1 && p.stencil_tps != 4) { err = "stencil_tps must be 0, 1 or 4"; return OVL_EINVAL; }
+    if (p.sap_tps != 0 && p.sap_tps != 1 && p.sap_tps != 2 && p.sap_tps != 4) { err = "sap_tps must be 0, 1, 2 or 4"; return OVL_EINVAL; }
     for (int m = 0; m < 4 && p.precond != OVL_PREC_NONE; m++) {
         if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m]) {
             err = "sap_block must be even and divide the lattice extent";
@@ -345,15 +348,16 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
     Ctx *c = this;
     int iters = 0;
     const float4 *y;
-    if (p.precision == OVL_MIXED_HALF) {
-        // shifted directions stored in FP16 (per site: 48 B + 4 B norm read and written)
+    if (p.precision == OVL_MIXED_HALF || p.precision == OVL_MIXED_BF16) {
+        // shifted directions stored in 16 bits (per site: 48 B, + 4 B norm for FP16, read and written)
+        const bool bf = p.precision == OVL_MIXED_BF16;
         ST(ensure_msh());
         ST(ms_setup(msh_state, tol));
-        CK(ms_init_half(g, npole, msh_state, msh, b, rs, stream));
+        CK(ms_init_half(g, npole, msh_state, msh, b, rs, bf, stream));
         auto fn = [&](cudaEvent_t *e, unsigned f) {
-            return ms_iter_half(g, U32, (float)m0_ker, msh_state, msh, rs, stream, e, f);
+            return ms_iter_half(g, U32, (float)m0_ker, msh_state, msh, rs, bf, stream, e, f);
         };
-        ST(ms_run(msh_state, 1, 2, 104.0, fn, &iters));
+        ST(ms_run(msh_state, 1, 2, bf ? 96.0 : 104.0, fn, &iters));
         y = msh.y;
     } else {
         ST(ensure_ms32());
@@ -718,6 +722,7 @@ ovl_status Ctx::sigma_min_estimate(double *smin) {
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <array>
 static std::mutex g_tune_mu;
 struct TuneEntry {
     int tps64, tps32;
@@ -775,6 +780,66 @@ ovl_status Ctx::autotune() {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         TuneEntry te{g.tps64, g.tps32, {tune_ms[0], tune_ms[1], tune_ms[2], tune_ms[3]}};
         g_tune_cache[key] = te;
+    }
+    cudaFree(buf);
+    allocs.erase(std::find(allocs.begin(), allocs.end(), buf));
+    return OVL_OK;
+}
+
+// Threads per site of the FP32 Schwarz block kernel (1, 2 or 4): one Schwarz cycle of
+// each variant is timed on a constant non-zero input and the fastest kept. Cached per
+// process, lattice shape and block shape.
+static std::map<std::tuple<int, int, int, int, int, int, int, int, int>, std::pair<int, std::array<float, 3>>>
+    g_sap_cache;
+
+ovl_status Ctx::autotune_sap() {
+    Ctx *c = this;
+    const auto key = std::make_tuple(g.L[0], g.L[1], g.L[2], g.L[3], p.sap_block[0], p.sap_block[1], p.sap_block[2],
+                                     p.sap_block[3], p.sap_mr_iters);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_sap_cache.find(key);
+        if (it != g_sap_cache.end()) {
+            sap_tps = it->second.first;
+            for (int k = 0; k < 3; k++) sap_ms[k] = it->second.second[k];
+            return OVL_OK;
+        }
+    }
+    void *buf;
+    const size_t bytes = (size_t)n64 * sizeof(float);
+    ST(alloc(&buf, bytes * 3));
+    float4 *fv = (float4 *)buf, *fx = (float4 *)((char *)buf + bytes), *fr = (float4 *)((char *)buf + 2 * bytes);
+    CK(cudaMemsetAsync(fv, 0x3c, bytes, stream));   // every float 0x3c3c3c3c ~ 0.0115
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int reps = g.V >= (1 << 20) ? 3 : 10;
+    const int tps_of[3] = {1, 2, 4};
+    float best = 0.f;
+    int best_tps = 1;
+    for (int v = 0; v < 3; v++) {
+        SapGeom sg = make_sap_geom(g, p.sap_block);
+        sg.tps = tps_of[v];
+        for (int k = 0; k < 2 + reps; k++) {
+            if (k == 2) CK(cudaEventRecord(e0, stream));
+            CK(sap_f32(g, sg, U32, fv, fx, fr, -0.5f, 1, p.sap_mr_iters, stream));
+        }
+        CK(cudaEventRecord(e1, stream));
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        sap_ms[v] = ms / reps;
+        if (v == 0 || sap_ms[v] < best) {
+            best = sap_ms[v];
+            best_tps = tps_of[v];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    sap_tps = best_tps;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_sap_cache[key] = {sap_tps, {sap_ms[0], sap_ms[1], sap_ms[2]}};
     }
     cudaFree(buf);
     allocs.erase(std::find(allocs.begin(), allocs.end(), buf));
@@ -901,6 +966,13 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
     c->g.tps64 = c->g.tps32 = 1;
     if (c->p.stencil_tps) c->g.tps64 = c->g.tps32 = c->p.stencil_tps;
     else ST(c->autotune());
+    if (c->p.sap_tps) {
+        c->sap_tps = c->p.sap_tps;
+        c->sap_tuned = true;
+    } else if (c->p.precond != OVL_PREC_NONE) {
+        ST(c->autotune_sap());
+        c->sap_tuned = true;
+    }
     // spectral interval of |Q|
     if (c->p.lambda_min > 0) {
         c->lam_min = c->p.lambda_min;
@@ -1071,6 +1143,15 @@ extern "C" ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, flo
     return OVL_OK;
 }
 
+extern "C" ovl_status ovl_tuning_sap(const ovl_ctx *ctx, int *tps, float *ms) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c) return OVL_EINVAL;
+    if (tps) *tps = c->sap_tps;
+    if (ms)
+        for (int k = 0; k < 3; k++) ms[k] = c->sap_ms[k];
+    return OVL_OK;
+}
+
 extern "C" ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, double m0, double tol, int *iters) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     ST(check_ctx_ptrs(c, x, b));
@@ -1088,6 +1169,10 @@ extern "C" ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, dou
             c->err = "sap_block must be even, divide the lattice extent and hold <= 256 sites";
             return OVL_EINVAL;
         }
+    }
+    if (!c->sap_tuned) {
+        ST(c->autotune_sap());
+        c->sap_tuned = true;
     }
     ST(c->import_vec(b, c->io_a));
     int it = 0;

@@ -18,13 +18,14 @@ struct StoreFin2 {
 };
 
 // Per-thread partial sums are kept in the vector's own precision T (a grid-stride
-// thread sees only a few elements); blocks and the grid are summed in FP64.
+// thread sees only a few elements), and so are the warp sums; warps, blocks and the grid
+// are summed in FP64.
 template <typename T>
 __global__ void k_norm2(const T *__restrict__ x, long n, RedScratch rs, double *res) {
     T a = 0;
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
         a += x[k] * x[k];
-    double v[1] = {(double)a};
+    T v[1] = {a};
     grid_reduce<1>(v, rs, StoreFin1{res});
 }
 
@@ -38,7 +39,7 @@ __global__ void k_cdot(const T *__restrict__ x, const T *__restrict__ y, long nc
         a += xr * yr + xi * yi;
         b += xr * yi - xi * yr;
     }
-    double v[2] = {(double)a, (double)b};
+    T v[2] = {a, b};
     grid_reduce<2>(v, rs, StoreFin2{res});
 }
 
@@ -70,8 +71,9 @@ __global__ void k_multidot_part(const T *__restrict__ base, long stride, const T
         a += vr * wr + vi * wi;
         b += vr * wi - vi * wr;
     }
-    double s[2] = {(double)a, (double)b};
-    block_sum<2>(s);
+    const T t[2] = {a, b};
+    double s[2];
+    block_sum<2>(t, s);
     if (threadIdx.x == 0) {
         partials[((long)blockIdx.y * gridDim.x + blockIdx.x) * 2] = s[0];
         partials[((long)blockIdx.y * gridDim.x + blockIdx.x) * 2 + 1] = s[1];

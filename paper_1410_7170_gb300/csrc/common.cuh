@@ -8,6 +8,7 @@
 //   FP64 spinor: double2 [p][12 spin-colour][Vh]         (192 B per site)
 //   FP32 spinor: float4  [p][6 pairs of spin-colour][Vh] ( 96 B per site)
 //   FP16 spinor: uint4 (8 halves) [p][3][Vh] + float norm [p][Vh] (48+4 B per site)
+//   BF16 spinor: uint4 (8 bfloat16) [p][3][Vh], no norm              (48 B per site)
 //   FP64 link:   double2 [p][mu][9][Vh]   all 18 reals of U_mu(x)
 //   FP32 link:   float4  [p][mu][3][Vh]   rows 0 and 1 (12 reals)
 // The FP32 stencils rebuild row 2 of an SU(3) link in registers as conj(row0 x row1);
@@ -16,6 +17,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace ovl {
@@ -182,6 +184,45 @@ __device__ __forceinline__ void store_spinor(HalfSpinor f, int Vh, int p, int i,
         b[(size_t)c * Vh] = make_uint4(u[0], u[1], u[2], u[3]);
     }
     f.norm[(size_t)p * Vh + i] = m;
+}
+
+// BF16 spinor: 24 bfloat16 per site in 3 uint4 words, no scale (BF16 keeps the FP32
+// exponent range; 8 significant bits against FP16's 11).
+struct Bf16Spinor {
+    uint4 *v;
+};
+struct Bf16SpinorC {
+    const uint4 *v;
+};
+
+template <typename R>
+__device__ __forceinline__ void load_spinor(Bf16SpinorC f, int Vh, int p, int i, cpx<R> s[12]) {
+    const uint4 *b = f.v + (size_t)p * 3 * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        uint4 w = __ldg(b + (size_t)c * Vh);
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&u[q]);
+            float2 fl = __bfloat1622float2(h);
+            s[4 * c + q] = cpx<R>{(R)fl.x, (R)fl.y};
+        }
+    }
+}
+template <typename R>
+__device__ __forceinline__ void store_spinor(Bf16Spinor f, int Vh, int p, int i, const cpx<R> s[12]) {
+    uint4 *b = f.v + (size_t)p * 3 * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        uint32_t u[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            __nv_bfloat162 h = __floats2bfloat162_rn((float)s[4 * c + q].re, (float)s[4 * c + q].im);
+            u[q] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        b[(size_t)c * Vh] = make_uint4(u[0], u[1], u[2], u[3]);
+    }
 }
 
 // Links: rows 0 and 1 stored, row 2 = conj(row0 x row1).

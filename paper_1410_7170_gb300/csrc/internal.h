@@ -171,9 +171,9 @@ cudaError_t ms_init_f32(const Geom &g, int n, MsState *s, MsVectors<float4> v, c
                         cudaStream_t st);
 cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, MsVectors<float4> v,
                         RedScratch rs, cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
-cudaError_t ms_init_half(const Geom &g, int n, MsState *s, MsVectorsH v, const float4 *b, RedScratch rs,
+cudaError_t ms_init_half(const Geom &g, int n, MsState *s, MsVectorsH v, const float4 *b, RedScratch rs, bool bf16,
                          cudaStream_t st);
-cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, MsVectorsH v, RedScratch rs,
+cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, MsVectorsH v, RedScratch rs, bool bf16,
                          cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
 
 // ---------------------------------------------------------------- several right-hand sides

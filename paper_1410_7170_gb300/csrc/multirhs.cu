@@ -49,19 +49,24 @@ __global__ void __launch_bounds__(384) k_wilson_mrhs(Geom g, const LT *__restric
 }
 
 // Per-right-hand-side grid reduction: warp y of every block holds the partial sums of
-// right-hand side y; the last block sums each row in block order and warp y runs
-// fin(rhs, total, lane). partials: [nrhs][NV][kMaxRedBlocks].
-template <int NV, typename Fin>
-__device__ __forceinline__ void grid_reduce_rows(double v[NV], RedScratch rs, int nrhs, Fin fin) {
+// right-hand side y (in T: FP32 kernels sum their warps in FP32); the last block sums each
+// row in block order in FP64 and warp y runs fin(rhs, total, lane).
+// partials: [nrhs][NV][kMaxRedBlocks].
+template <int NV, typename T, typename Fin>
+__device__ __forceinline__ void grid_reduce_rows(const T vt[NV], RedScratch rs, int nrhs, Fin fin) {
     __shared__ int is_last;
     const int y = threadIdx.y, lane = threadIdx.x;
+    T v[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++)
+    for (int k = 0; k < NV; k++) {
+        v[k] = vt[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    }
     if (lane == 0 && y < nrhs)
 #pragma unroll
-        for (int k = 0; k < NV; k++) rs.partials[((size_t)y * NV + k) * kMaxRedBlocks + blockIdx.x] = v[k];
+        for (int k = 0; k < NV; k++)
+            rs.partials[((size_t)y * NV + k) * kMaxRedBlocks + blockIdx.x] = (double)v[k];
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         __threadfence();
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(384) k_msb_q(Geom g, const LT *__restrict__ U,
                                                long stride, RedScratch rs) {
     const int y = threadIdx.y;
     const bool live = y < nrhs && !st[y].done;
-    double v[2] = {0.0, 0.0};
+    R v[2] = {0, 0};
     if (live) {
         const ST *x = p0 + y * pstride;
         for (int k = tile_site(blockIdx.x); k < g.V; k += gridDim.x * kTile) {
@@ -182,8 +187,8 @@ __global__ void __launch_bounds__(384) k_msb_q(Geom g, const LT *__restrict__ U,
                 a0 += norm2(res[c]);
                 a1 += norm2(own[c]);
             }
-            v[0] += (double)a0;
-            v[1] += (double)a1;
+            v[0] += a0;
+            v[1] += a1;
         }
     }
     grid_reduce_rows<2>(v, rs, nrhs, AlphaFinB{st});
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(384) k_msb_r(Geom g, const LT *__restrict__ U,
                                                ST *__restrict__ r, long stride, RedScratch rs) {
     const int y = threadIdx.y;
     const bool live = y < nrhs && !st[y].done;
-    double v[1] = {0.0};
+    R v[1] = {0};
     if (live) {
         const R alpha = (R)st[y].alpha, sig0 = (R)st[y].sigma[0];
         const ST *tt = t + y * stride, *pp = p0 + y * pstride;
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(384) k_msb_r(Geom g, const LT *__restrict__ U,
                 rv[c] = rv[c] - alpha * (res[c] + sig0 * pv[c]);
                 a0 += norm2(rv[c]);
             }
-            v[0] += (double)a0;
+            v[0] += a0;
             store_spinor<R>(rr, g.Vh, p, i, rv);
         }
     }
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(384) k_msb_init(MsState *st, int nrhs, int npo
     using A = typename WordB<ST>::A;
     constexpr int N = WordB<ST>::N;
     const int y = threadIdx.y;
-    double v[1] = {0.0};
+    A v[1] = {0};
     if (y < nrhs) {
         for (long k = (long)blockIdx.x * kTile + threadIdx.x; k < stride; k += (long)gridDim.x * kTile) {
             const ST w = b[y * stride + k];
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(384) k_msb_init(MsState *st, int nrhs, int npo
             WordB<ST>::get(w, e);
 #pragma unroll
             for (int q = 0; q < N; q++) a += e[q] * e[q];
-            v[0] += (double)a;
+            v[0] += a;
         }
     }
     grid_reduce_rows<1>(v, rs, nrhs, InitFinB{st});

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, co
                                                  const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs,
                                                  int spb) {
     if (s->done) return;
-    double v[2] = {0.0, 0.0};
+    R v[2] = {0, 0};   // per-thread sums in R; FP64 from the warp sums on (grid_reduce)
     const bool lane_has_sites = threadIdx.x < spb;
     for (int k = blockIdx.x * spb + threadIdx.x; lane_has_sites && k < g.V; k += gridDim.x * spb) {
         int p, i;
@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, co
             a0 += norm2(res[c]);
             a1 += norm2(own[c]);
         }
-        v[0] += (double)a0;
-        v[1] += (double)a1;
+        v[0] += a0;
+        v[1] += a1;
     }
     grid_reduce<2>(v, rs, AlphaFin{s});
 }
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r(Geom g, co
                                                  ST *__restrict__ r, RedScratch rs, int spb) {
     if (s->done) return;
     const R alpha = (R)s->alpha, sig0 = (R)s->sigma[0];
-    double v[1] = {0.0};
+    R v[1] = {0};
     const bool lane_has_sites = threadIdx.x < spb;
     for (int k = blockIdx.x * spb + threadIdx.x; lane_has_sites && k < g.V; k += gridDim.x * spb) {
         int p, i;
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r(Geom g, co
             rv[c] = rv[c] - alpha * (res[c] + sig0 * pp[c]);
             a0 += norm2(rv[c]);
         }
-        v[0] += (double)a0;
+        v[0] += a0;
         store_spinor<R>(r, g.Vh, p, i, rv);
     }
     grid_reduce_warp<1>(v, rs, ShiftFin{s});
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q4(Geom g, c
                                                   const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs) {
     if (s->done) return;
     using C = Chunk<ST>;
-    double v[2] = {0.0, 0.0};
+    R v[2] = {0, 0};
     const long nthr = 4L * g.V;
     for (long base = (long)blockIdx.x * blockDim.x; base < nthr; base += (long)gridDim.x * blockDim.x) {
         const long tt = base + threadIdx.x;
@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q4(Geom g, c
                 a0 += norm2(res[e]);
                 a1 += norm2(own[e]);
             }
-            v[0] += (double)a0;
-            v[1] += (double)a1;
+            v[0] += a0;
+            v[1] += a1;
             C::template store<R>(t, g.Vh, p, i, j, res);
         }
     }
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r4(Geom g, c
     if (s->done) return;
     using C = Chunk<ST>;
     const R alpha = (R)s->alpha, sig0 = (R)s->sigma[0];
-    double v[1] = {0.0};
+    R v[1] = {0};
     const long nthr = 4L * g.V;
     for (long base = (long)blockIdx.x * blockDim.x; base < nthr; base += (long)gridDim.x * blockDim.x) {
         const long tt = base + threadIdx.x;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r4(Geom g, c
                 rv[e] = rv[e] - alpha * (res + sig0 * pp[e]);
                 a0 += norm2(rv[e]);
             }
-            v[0] += (double)a0;
+            v[0] += a0;
             C::template store<R>(r, g.Vh, p, i, j, rv);
         }
     }
@@ -343,7 +343,7 @@ template <typename ST>
 __global__ void k_ms_init(MsState *s, const ST *__restrict__ b, ST *r, ST *y, ST *P, long stride, long nw,
                           int n, RedScratch rs) {
     constexpr int N = Word<ST>::N;
-    double v[1] = {0.0};
+    typename Word<ST>::A v[1] = {0};
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (long)gridDim.x * blockDim.x) {
         const ST w = b[k];
         r[k] = w;
@@ -353,7 +353,7 @@ __global__ void k_ms_init(MsState *s, const ST *__restrict__ b, ST *r, ST *y, ST
         Word<ST>::get(w, e);
 #pragma unroll
         for (int q = 0; q < N; q++) a += e[q] * e[q];
-        v[0] += (double)a;
+        v[0] += a;
     }
     grid_reduce<1>(v, rs, InitFin{s});
 }
@@ -365,9 +365,24 @@ inline int stream_grid(long n) {
     return (int)(b < 1 ? 1 : b);
 }
 
-// ---- FP16-stored shifted directions (one thread per site: the FP16 words share a norm)
+// ---- 16-bit shifted directions (one thread per site: the FP16 words share a norm)
 // y += sum_l w_l a^l p_l ; p_l = zeta_l r + b^l p_l, with p_0 in FP32 and p_l (l >= 1)
-// in FP16; the last block retires finished shifts as k_ms_shifts does.
+// in FP16 with a per-site scale (BF = false) or in BF16 (BF = true); the last block
+// retires finished shifts as k_ms_shifts does.
+template <bool BF>
+__device__ __forceinline__ void load_p16(const MsVectorsH &v, int l, int Vh, int p, int i, cpx<float> pv[12]) {
+    if (BF) load_spinor<float>(Bf16SpinorC{v.ph + (size_t)(l - 1) * v.words_h}, Vh, p, i, pv);
+    else load_spinor<float>(HalfSpinorC{v.ph + (size_t)(l - 1) * v.words_h, v.pn + (size_t)(l - 1) * 2 * Vh}, Vh, p,
+                            i, pv);
+}
+template <bool BF>
+__device__ __forceinline__ void store_p16(const MsVectorsH &v, int l, int Vh, int p, int i, const cpx<float> pv[12]) {
+    if (BF) store_spinor<float>(Bf16Spinor{v.ph + (size_t)(l - 1) * v.words_h}, Vh, p, i, pv);
+    else store_spinor<float>(HalfSpinor{v.ph + (size_t)(l - 1) * v.words_h, v.pn + (size_t)(l - 1) * 2 * Vh}, Vh, p,
+                             i, pv);
+}
+
+template <bool BF>
 __global__ void __launch_bounds__(kBlock) k_ms_shifts_half(Geom g, MsState *s, MsVectorsH v, unsigned *counter) {
     __shared__ float sw[kMaxPoles], sz[kMaxPoles], sb[kMaxPoles];
     __shared__ int sidx[kMaxPoles];
@@ -397,20 +412,15 @@ __global__ void __launch_bounds__(kBlock) k_ms_shifts_half(Geom g, MsState *s, M
         for (int a = 0; a < na; a++) {
             const int l = sidx[a];
             const float wl = sw[a], zl = sz[a], bl = sb[a];
-            if (l == 0) {
-                load_spinor<float>(v.p0, g.Vh, p, i, pv);
-            } else {
-                load_spinor<float>(HalfSpinorC{v.ph + (size_t)(l - 1) * v.words_h, v.pn + (size_t)(l - 1) * g.V},
-                                   g.Vh, p, i, pv);
-            }
+            if (l == 0) load_spinor<float>(v.p0, g.Vh, p, i, pv);
+            else load_p16<BF>(v, l, g.Vh, p, i, pv);
 #pragma unroll
             for (int c = 0; c < 12; c++) {
                 yv[c] = yv[c] + wl * pv[c];
                 pv[c] = zl * rv[c] + bl * pv[c];
             }
             if (l == 0) store_spinor<float>(v.p0, g.Vh, p, i, pv);
-            else store_spinor<float>(HalfSpinor{v.ph + (size_t)(l - 1) * v.words_h, v.pn + (size_t)(l - 1) * g.V},
-                                     g.Vh, p, i, pv);
+            else store_p16<BF>(v, l, g.Vh, p, i, pv);
         }
         store_spinor<float>(v.y, g.Vh, p, i, yv);
     }
@@ -422,9 +432,10 @@ __global__ void __launch_bounds__(kBlock) k_ms_shifts_half(Geom g, MsState *s, M
     }
 }
 
-// r = y = p_0 = b in FP32, p_l = b in FP16 (l >= 1) ; ||b||^2
+// r = y = p_0 = b in FP32, p_l = b in FP16 or BF16 (l >= 1) ; ||b||^2
+template <bool BF>
 __global__ void k_ms_init_half(Geom g, MsState *s, MsVectorsH v, const float4 *__restrict__ b, int n, RedScratch rs) {
-    double acc[1] = {0.0};
+    float acc[1] = {0.f};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.V; k += gridDim.x * blockDim.x) {
         const int p = k >= g.Vh, i = k - p * g.Vh;
         cpx<float> bv[12];
@@ -432,13 +443,11 @@ __global__ void k_ms_init_half(Geom g, MsState *s, MsVectorsH v, const float4 *_
         store_spinor<float>(v.r, g.Vh, p, i, bv);
         store_spinor<float>(v.y, g.Vh, p, i, bv);
         store_spinor<float>(v.p0, g.Vh, p, i, bv);
-        for (int l = 1; l < n; l++)
-            store_spinor<float>(HalfSpinor{v.ph + (size_t)(l - 1) * v.words_h, v.pn + (size_t)(l - 1) * g.V}, g.Vh, p,
-                                i, bv);
+        for (int l = 1; l < n; l++) store_p16<BF>(v, l, g.Vh, p, i, bv);
         float a = 0.f;
 #pragma unroll
         for (int c = 0; c < 12; c++) a += norm2(bv[c]);
-        acc[0] += (double)a;
+        acc[0] += a;
     }
     grid_reduce<1>(acc, rs, InitFin{s});
 }
@@ -489,13 +498,14 @@ cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, Ms
 }  // namespace ovl
 
 namespace ovl {
-cudaError_t ms_init_half(const Geom &g, int n, MsState *s, MsVectorsH v, const float4 *b, RedScratch rs,
+cudaError_t ms_init_half(const Geom &g, int n, MsState *s, MsVectorsH v, const float4 *b, RedScratch rs, bool bf16,
                          cudaStream_t st) {
-    k_ms_init_half<<<red_grid(g.V), kBlock, 0, st>>>(g, s, v, b, n, rs);
+    if (bf16) k_ms_init_half<true><<<red_grid(g.V), kBlock, 0, st>>>(g, s, v, b, n, rs);
+    else k_ms_init_half<false><<<red_grid(g.V), kBlock, 0, st>>>(g, s, v, b, n, rs);
     count_launches(1);
     return cudaGetLastError();
 }
-cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, MsVectorsH v, RedScratch rs,
+cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, MsVectorsH v, RedScratch rs, bool bf16,
                          cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
     const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<float>::value, kMaxRedBlocks);
     cudaError_t e;
@@ -504,7 +514,9 @@ cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, M
     if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
     k_ms_r<float, float4, float4><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + 4.f, s, v.t, v.p0, v.r, rs, ls.spb);
     if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
-    k_ms_shifts_half<<<balanced_shape(g.V, g.nsm, 2, 1 << 30).grid, kBlock, 0, st>>>(g, s, v, rs.counter);
+    const int gsh = balanced_shape(g.V, g.nsm, 2, 1 << 30).grid;
+    if (bf16) k_ms_shifts_half<true><<<gsh, kBlock, 0, st>>>(g, s, v, rs.counter);
+    else k_ms_shifts_half<false><<<gsh, kBlock, 0, st>>>(g, s, v, rs.counter);
     if (ev && (e = cudaEventRecordWithFlags(ev[3], st, ev_flags)) != cudaSuccess) return e;
     count_launches(3);
     return cudaGetLastError();

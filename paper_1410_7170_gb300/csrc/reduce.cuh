@@ -35,12 +35,47 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
     }
 }
 
-// Reduce v[NV] over the grid; the last block calls fin(total) on thread 0 and
-// resets the counter. Must be reached by every thread of every block.
-template <int NV, typename Fin>
-__device__ __forceinline__ void grid_reduce(double v[NV], RedScratch rs, Fin fin) {
-    __shared__ int is_last;
+// Block-wide sum of per-thread FP32 values: the warp stage in FP32 (shuffles), the sum
+// over warps in FP64 by the first warp; the FP64 result is valid in thread 0. GB300 runs
+// FP64 at 1/64 of its FP32 rate, so FP64 work stays at one warp per block.
+template <int NV>
+__device__ __forceinline__ void block_sum(const float vf[NV], double v[NV]) {
+    __shared__ double sm[NV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    float t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        t[k] = vf[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], off);
+    }
+    __syncthreads();   // protect sm from a previous use in the same kernel
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) sm[k][warp] = (double)t[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) v[k] = lane < nw ? sm[k][lane] : 0.0;
+        warp_sum<NV>(v);
+    }
+}
+template <int NV>
+__device__ __forceinline__ void block_sum(const double vd[NV], double v[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = vd[k];
     block_sum<NV>(v);
+}
+
+// Reduce v[NV] (per-thread FP64 or FP32 partial sums) over the grid; the last block calls
+// fin(total) on thread 0 and resets the counter. Must be reached by every thread of every
+// block.
+template <int NV, typename T, typename Fin>
+__device__ __forceinline__ void grid_reduce(const T vt[NV], RedScratch rs, Fin fin) {
+    __shared__ int is_last;
+    double v[NV];
+    block_sum<NV>(vt, v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; k++) rs.partials[k * kMaxRedBlocks + blockIdx.x] = v[k];
@@ -68,11 +103,12 @@ __device__ __forceinline__ void grid_reduce(double v[NV], RedScratch rs, Fin fin
 
 // As grid_reduce, but the last block runs fin(total, lane) on all 32 lanes of its first
 // warp (for finalisations that are parallel over a small index, e.g. one lane per shift).
-template <int NV, typename Fin>
-__device__ __forceinline__ void grid_reduce_warp(double v[NV], RedScratch rs, Fin fin) {
+template <int NV, typename T, typename Fin>
+__device__ __forceinline__ void grid_reduce_warp(const T vt[NV], RedScratch rs, Fin fin) {
     __shared__ int is_last;
     __shared__ double tot[NV];
-    block_sum<NV>(v);
+    double v[NV];
+    block_sum<NV>(vt, v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; k++) rs.partials[k * kMaxRedBlocks + blockIdx.x] = v[k];

@@ -92,20 +92,42 @@ __device__ __forceinline__ void block_apply(const R *s, const R *u, int nb, int 
     wilson_combine<R>(m4, own, acc, q);
 }
 
+// MR step of a block solve: the block sums of Re<q, s>, Im<q, s> and |q|^2 (per warp by
+// shuffles, then over warps in a fixed order by thread 0, all in R) and alpha = <q, s>/|q|^2,
+// computed once by thread 0 and broadcast. Returns false when |q|^2 is not positive
+// (uniform over the CTA). Every thread of the CTA must call it.
 template <typename R>
-__device__ __forceinline__ void block_sum_sh(double v[3], double *sh) {
-    // block-wide sum of 3 doubles, result broadcast to every thread via sh[0..2]
-    block_sum<3>(v);
-    if (threadIdx.x == 0) {
-        sh[0] = v[0];
-        sh[1] = v[1];
-        sh[2] = v[2];
+__device__ __forceinline__ bool mr_alpha(R a0, R a1, R a2, cpx<R> &alpha) {
+    __shared__ R red[3][32];
+    __shared__ R bc[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a0 += __shfl_down_sync(0xffffffffu, a0, off);
+        a1 += __shfl_down_sync(0xffffffffu, a1, off);
+        a2 += __shfl_down_sync(0xffffffffu, a2, off);
+    }
+    if (lane == 0) {
+        red[0][warp] = a0;
+        red[1][warp] = a1;
+        red[2][warp] = a2;
     }
     __syncthreads();
-    v[0] = sh[0];
-    v[1] = sh[1];
-    v[2] = sh[2];
+    if (threadIdx.x == 0) {
+        R s0 = 0, s1 = 0, s2 = 0;
+        for (int w = 0; w < nw; w++) {
+            s0 += red[0][w];
+            s1 += red[1][w];
+            s2 += red[2][w];
+        }
+        const bool ok = s2 > (R)0;
+        bc[0] = ok ? s0 / s2 : (R)0;
+        bc[1] = ok ? s1 / s2 : (R)0;
+        bc[2] = ok ? (R)1 : (R)0;
+    }
     __syncthreads();
+    alpha = cpx<R>{bc[0], bc[1]};
+    return bc[2] > (R)0;
 }
 
 // One CTA per block of the given colour.
@@ -119,7 +141,6 @@ template <typename R, typename LT, typename ST, bool RES>
 __global__ void __launch_bounds__(kBlock, SapMinBlocks<R>::value) k_sap_block(Geom g, SapGeom sg, const LT *__restrict__ U, const ST *__restrict__ v, ST *x, R m4,
                             int colour, int mr_iters, bool colour_grid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double sh[3];
     const int nb = sg.nb;
     // block coordinates of this CTA
     int B[4], rem = blockIdx.x;
@@ -188,18 +209,15 @@ __global__ void __launch_bounds__(kBlock, SapMinBlocks<R>::value) k_sap_block(Ge
         if (act) sm_store_sp(s, nb, t, res);
         __syncthreads();
         if (act) block_apply<R>(s, u, nb, t, l, sg.b, sg.stride, m4, q);
-        R a0 = 0, a1 = 0, a2 = 0;   // per-site sums in the arithmetic type, block sums in FP64
+        R a0 = 0, a1 = 0, a2 = 0;   // per-site and block sums in the arithmetic type
 #pragma unroll
         for (int c = 0; c < 12; c++) {
             a0 += q[c].re * res[c].re + q[c].im * res[c].im;   // Re <q, s>
             a1 += q[c].re * res[c].im - q[c].im * res[c].re;   // Im <q, s>
             a2 += norm2(q[c]);
         }
-        double v[3] = {(double)a0, (double)a1, (double)a2};
-        block_sum_sh<R>(v, sh);
-        if (!(v[2] > 0.0)) break;   // uniform: every thread holds the block sums
-        __syncthreads();            // smem s is rewritten at the top of the next step
-        const cpx<R> alpha = cpx<R>{(R)(v[0] / v[2]), (R)(v[1] / v[2])};
+        cpx<R> alpha;
+        if (!mr_alpha<R>(a0, a1, a2, alpha)) break;   // uniform over the CTA
 #pragma unroll
         for (int c = 0; c < 12; c++) {
             e[c] = e[c] + alpha * res[c];
@@ -215,35 +233,307 @@ __global__ void __launch_bounds__(kBlock, SapMinBlocks<R>::value) k_sap_block(Ge
     store_spinor<R>(x, g.Vh, p, i, xv);
 }
 
+// ---------------------------------------------------------------------------------
+// Several threads per block site (TPS = 2 or 4). At 16^4 a colour has only 128 blocks of
+// 4^4 sites, so the one-thread-per-site kernel runs 8 warps on an SM and the MR loop is
+// latency-bound; here thread (k, site) of the CTA, k = threadIdx.x / nbp warp-uniform,
+// computes the hops of the directions mu in [k*4/TPS, (k+1)*4/TPS) and owns the C =
+// 12/TPS spin-colour components [k*C, (k+1)*C) of the MR state. The partial hopping sums
+// are combined through shared memory, summed over k in a fixed order (deterministic).
+
+// The two block-local hops of direction MU (hops that leave the block are dropped).
+template <int MU, typename R>
+__device__ __forceinline__ void block_hop_dir(const R *s, const R *u, int nb, int t, const int l[4], const int bx[4],
+                                              const int stride[4], cpx<R> acc[12]) {
+    if (l[MU] + 1 < bx[MU]) {
+        cpx<R> v[12], h0[3], h1[3], a0[3], a1[3], m[3][3];
+        sm_load_sp(s, nb, t + stride[MU], v);
+        sm_load_link(u, nb, MU, t, m);
+        proj_fwd(MU, v, h0, h1);
+        su3_mul(m, h0, a0);
+        su3_mul(m, h1, a1);
+        acc_fwd<false>(MU, acc, a0, a1);
+    }
+    if (l[MU] > 0) {
+        cpx<R> v[12], h0[3], h1[3], a0[3], a1[3], m[3][3];
+        sm_load_sp(s, nb, t - stride[MU], v);
+        sm_load_link(u, nb, MU, t - stride[MU], m);
+        proj_bwd(MU, v, h0, h1);
+        su3_dag_mul(m, h0, a0);
+        su3_dag_mul(m, h1, a1);
+        acc_bwd(MU, acc, a0, a1);
+    }
+}
+
+template <int TPS, typename R>
+__device__ __forceinline__ void block_hop_part(int k, const R *s, const R *u, int nb, int t, const int l[4],
+                                               const int bx[4], const int stride[4], cpx<R> acc[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = cpx<R>{0, 0};
+    if (TPS == 2) {
+        if (k == 0) {
+            block_hop_dir<0>(s, u, nb, t, l, bx, stride, acc);
+            block_hop_dir<1>(s, u, nb, t, l, bx, stride, acc);
+        } else {
+            block_hop_dir<2>(s, u, nb, t, l, bx, stride, acc);
+            block_hop_dir<3>(s, u, nb, t, l, bx, stride, acc);
+        }
+    } else {
+        switch (k) {
+            case 0: block_hop_dir<0>(s, u, nb, t, l, bx, stride, acc); break;
+            case 1: block_hop_dir<1>(s, u, nb, t, l, bx, stride, acc); break;
+            case 2: block_hop_dir<2>(s, u, nb, t, l, bx, stride, acc); break;
+            default: block_hop_dir<3>(s, u, nb, t, l, bx, stride, acc); break;
+        }
+    }
+}
+
+// The hops of this thread's directions on the whole lattice (global memory).
+template <int TPS, typename R, typename LT, typename ST>
+__device__ __forceinline__ void glob_hop_part(int k, const Geom &g, const LT *__restrict__ U, ST in, int p, int i,
+                                              const int x[4], cpx<R> acc[12]) {
+    if (TPS == 2) {
+        if (k == 0) {
+            hop_dir<0, true, R>(g, U, in, p, i, x, acc);
+            hop_dir<1, false, R>(g, U, in, p, i, x, acc);
+        } else {
+            hop_dir<2, true, R>(g, U, in, p, i, x, acc);
+            hop_dir<3, false, R>(g, U, in, p, i, x, acc);
+        }
+    } else {
+        switch (k) {
+            case 0: hop_dir<0, true, R>(g, U, in, p, i, x, acc); break;
+            case 1: hop_dir<1, true, R>(g, U, in, p, i, x, acc); break;
+            case 2: hop_dir<2, true, R>(g, U, in, p, i, x, acc); break;
+            default: hop_dir<3, true, R>(g, U, in, p, i, x, acc); break;
+        }
+    }
+}
+
+// Components [c0, c0 + C) of site (p, i) of an FP32 spinor (complex c is float2 number
+// 2 * ((p * 6 + c / 2) * Vh + i) + c % 2 of the float4 array).
+template <int C>
+__device__ __forceinline__ void load_comps(const float4 *f, int Vh, int p, int i, int c0, cpx<float> o[C]) {
+    const float2 *f2 = reinterpret_cast<const float2 *>(f);
+#pragma unroll
+    for (int e = 0; e < C; e++) {
+        const int c = c0 + e;
+        const float2 w = f2[2 * ((size_t)(p * 6 + c / 2) * Vh + i) + (c & 1)];
+        o[e] = cpx<float>{w.x, w.y};
+    }
+}
+template <int C>
+__device__ __forceinline__ void store_comps(float4 *f, int Vh, int p, int i, int c0, const cpx<float> o[C]) {
+    float2 *f2 = reinterpret_cast<float2 *>(f);
+#pragma unroll
+    for (int e = 0; e < C; e++) {
+        const int c = c0 + e;
+        f2[2 * ((size_t)(p * 6 + c / 2) * Vh + i) + (c & 1)] = make_float2(o[e].re, o[e].im);
+    }
+}
+
+// Sum over the TPS partial hopping sums of this thread's components: every thread wrote
+// its acc[12] to X[k][24][nb]; component c0 + e of the site is summed over k in order.
+template <int TPS, int C, typename R>
+__device__ __forceinline__ void gather_part(const R *X, int nb, int t, int c0, cpx<R> h[C]) {
+#pragma unroll
+    for (int e = 0; e < C; e++) {
+        const int c = c0 + e;
+        R re = X[(2 * c) * nb + t], im = X[(2 * c + 1) * nb + t];
+#pragma unroll
+        for (int kk = 1; kk < TPS; kk++) {
+            re += X[((size_t)kk * 24 + 2 * c) * nb + t];
+            im += X[((size_t)kk * 24 + 2 * c + 1) * nb + t];
+        }
+        h[e] = cpx<R>{re, im};
+    }
+}
+template <typename R>
+__device__ __forceinline__ void scatter_part(R *X, int nb, int t, int k, const cpx<R> acc[12]) {
+    R *b = X + (size_t)k * 24 * nb + t;
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+        b[(2 * c) * nb] = acc[c].re;
+        b[(2 * c + 1) * nb] = acc[c].im;
+    }
+}
+
+// FP32 only (the FP64 state would not fit in shared memory for 4^4 blocks). The CTA has
+// TPS * nbp threads, nbp = nb rounded up to whole warps (at most 256 sites per block).
+template <int TPS, bool RES>
+__global__ void __launch_bounds__(256 * TPS, 1)
+    k_sap_block_mt(Geom g, SapGeom sg, const float4 *__restrict__ U, const float4 *__restrict__ v, float4 *x, float m4,
+                   int colour, int mr_iters, bool colour_grid) {
+    using R = float;
+    constexpr int C = 12 / TPS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nb = sg.nb;
+    const int nbp = (nb + 31) & ~31;
+    int B[4], rem = blockIdx.x;
+    if (colour_grid) {
+        const int h3 = sg.nblk[3] / 2;
+        const int b3h = rem % h3; rem /= h3;
+        B[2] = rem % sg.nblk[2]; rem /= sg.nblk[2];
+        B[1] = rem % sg.nblk[1];
+        B[0] = rem / sg.nblk[1];
+        B[3] = 2 * b3h + ((B[0] + B[1] + B[2] + colour) & 1);
+    } else {
+        B[3] = rem % sg.nblk[3]; rem /= sg.nblk[3];
+        B[2] = rem % sg.nblk[2]; rem /= sg.nblk[2];
+        B[1] = rem % sg.nblk[1];
+        B[0] = rem / sg.nblk[1];
+        if (((B[0] + B[1] + B[2] + B[3]) & 1) != colour) return;   // uniform over the CTA
+    }
+    R *s = reinterpret_cast<R *>(smem_raw);   // [24][nb] spinor of the block
+    R *u = s + 24 * nb;                        // [4][18][nb] forward links
+    R *X = u + 72 * nb;                        // [TPS][24][nb] partial hopping sums
+    const int k = threadIdx.x / nbp;           // warp-uniform
+    const int ts = threadIdx.x - k * nbp;
+    const bool act = ts < nb;
+    const int t = act ? ts : 0;
+    const int c0 = k * C;
+    int l[4], rr = t;
+    l[3] = rr % sg.b[3]; rr /= sg.b[3];
+    l[2] = rr % sg.b[2]; rr /= sg.b[2];
+    l[1] = rr % sg.b[1];
+    l[0] = rr / sg.b[1];
+    int xg[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) xg[mu] = B[mu] * sg.b[mu] + l[mu];
+    const int p = (xg[0] + xg[1] + xg[2] + xg[3]) & 1;
+    const int i = eo_index(g, xg);
+    if (act) {   // forward links of this thread's directions
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (mu * TPS / 4 != k) continue;
+            cpx<R> m[3][3];
+            load_link<R>(U, g.Vh, p, mu, i, m);
+            R *b = u + (size_t)mu * 18 * nb + t;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    b[(a * 6 + 2 * c) * nb] = m[a][c].re;
+                    b[(a * 6 + 2 * c + 1) * nb] = m[a][c].im;
+                }
+        }
+    }
+    cpx<R> res[C], e[C], q[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        e[c] = cpx<R>{0, 0};
+        res[c] = cpx<R>{0, 0};
+        q[c] = cpx<R>{0, 0};
+    }
+    if (act) load_comps<C>(v, g.Vh, p, i, c0, res);
+    if (RES) {   // res = v - D_W x at this site, own components
+        if (act) {
+            cpx<R> acc[12];
+            glob_hop_part<TPS, R>(k, g, U, x, p, i, xg, acc);
+            scatter_part(X, nb, t, k, acc);
+        }
+        __syncthreads();
+        if (act) {
+            cpx<R> hop[C], own[C];
+            gather_part<TPS, C>(X, nb, t, c0, hop);
+            load_comps<C>(x, g.Vh, p, i, c0, own);
+#pragma unroll
+            for (int c = 0; c < C; c++) res[c] = res[c] - (m4 * own[c] - (R)0.5 * hop[c]);
+        }
+    }
+    for (int it = 0; it < mr_iters; it++) {
+        if (act) {
+            R *b = s + (size_t)(2 * c0) * nb + t;
+#pragma unroll
+            for (int c = 0; c < C; c++) {
+                b[(2 * c) * nb] = res[c].re;
+                b[(2 * c + 1) * nb] = res[c].im;
+            }
+        }
+        __syncthreads();
+        if (act) {
+            cpx<R> acc[12];
+            block_hop_part<TPS>(k, s, u, nb, t, l, sg.b, sg.stride, acc);
+            scatter_part(X, nb, t, k, acc);
+        }
+        __syncthreads();
+        R a0 = 0, a1 = 0, a2 = 0;
+        if (act) {
+            cpx<R> hop[C];
+            gather_part<TPS, C>(X, nb, t, c0, hop);
+#pragma unroll
+            for (int c = 0; c < C; c++) {
+                q[c] = m4 * res[c] - (R)0.5 * hop[c];
+                a0 += q[c].re * res[c].re + q[c].im * res[c].im;   // Re <q, s>
+                a1 += q[c].re * res[c].im - q[c].im * res[c].re;   // Im <q, s>
+                a2 += norm2(q[c]);
+            }
+        }
+        cpx<R> alpha;
+        if (!mr_alpha<R>(a0, a1, a2, alpha)) break;   // uniform over the CTA
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            e[c] = e[c] + alpha * res[c];
+            res[c] = res[c] - alpha * q[c];
+        }
+    }
+    __syncthreads();   // every thread of the CTA has finished reading x before any writes it
+    if (!act) return;
+    cpx<R> xv[C];
+    load_comps<C>(x, g.Vh, p, i, c0, xv);
+#pragma unroll
+    for (int c = 0; c < C; c++) xv[c] = xv[c] + e[c];
+    store_comps<C>(x, g.Vh, p, i, c0, xv);
+}
+
 }  // namespace
+
+// Grants the dynamic shared memory of kernel f once per size (per process).
+template <typename K>
+static cudaError_t grant_smem(K f, size_t smem, size_t &granted) {
+    if (smem <= 48 * 1024 || smem <= granted) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    granted = smem;
+    return cudaSuccess;
+}
+
+// Launch of one colour's block solves: RES forms the block residual from x in the kernel.
+template <typename R, typename LT, typename ST, bool RES>
+static cudaError_t launch_blocks(const Geom &g, const SapGeom &sg, const LT *U, const ST *v, ST *x, R m4, int colour,
+                                 int mr_iters, bool even, int grid, cudaStream_t st) {
+    static size_t granted[3] = {0, 0, 0};
+    if constexpr (sizeof(R) == 4) {
+        if (sg.tps == 2 || sg.tps == 4) {
+            const int nbp = (sg.nb + 31) / 32 * 32;
+            const size_t smem = (size_t)sg.nb * (24 + 72 + 24 * sg.tps) * sizeof(R);
+            cudaError_t e;
+            if (sg.tps == 2) {
+                if ((e = grant_smem(k_sap_block_mt<2, RES>, smem, granted[1])) != cudaSuccess) return e;
+                k_sap_block_mt<2, RES><<<grid, 2 * nbp, smem, st>>>(g, sg, U, v, x, m4, colour, mr_iters, even);
+            } else {
+                if ((e = grant_smem(k_sap_block_mt<4, RES>, smem, granted[2])) != cudaSuccess) return e;
+                k_sap_block_mt<4, RES><<<grid, 4 * nbp, smem, st>>>(g, sg, U, v, x, m4, colour, mr_iters, even);
+            }
+            return cudaGetLastError();
+        }
+    }
+    const size_t smem = (size_t)sg.nb * (24 + 4 * 18) * sizeof(R);
+    cudaError_t e;
+    if ((e = grant_smem(k_sap_block<R, LT, ST, RES>, smem, granted[0])) != cudaSuccess) return e;
+    const int threads = (sg.nb + 31) / 32 * 32;
+    k_sap_block<R, LT, ST, RES><<<grid, threads, smem, st>>>(g, sg, U, v, x, m4, colour, mr_iters, even);
+    return cudaGetLastError();
+}
 
 template <typename R, typename LT, typename ST>
 static cudaError_t sap_t(const Geom &g, const SapGeom &sg, const LT *U, const ST *v, ST *x, ST *r, R m0,
                          int cycles, int mr_iters, cudaStream_t st,
                          cudaError_t (*wil)(const Geom &, const LT *, const ST *, ST *, R, int, R, const ST *, R,
                                             cudaStream_t)) {
-    const size_t smem = (size_t)sg.nb * (24 + 4 * 18) * sizeof(R);
-    static size_t attr_set[2][2] = {{0, 0}, {0, 0}};   // dynamic shared memory granted, per precision/variant
-    const int which = sizeof(R) == 8;
-    if (smem > 48 * 1024) {
-        cudaError_t e;
-        if (smem > attr_set[which][0]) {
-            if ((e = cudaFuncSetAttribute(k_sap_block<R, LT, ST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem)) != cudaSuccess) {
-                cudaGetLastError();
-                return e;
-            }
-            attr_set[which][0] = smem;
-        }
-        if (smem > attr_set[which][1]) {
-            if ((e = cudaFuncSetAttribute(k_sap_block<R, LT, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem)) != cudaSuccess) {
-                cudaGetLastError();
-                return e;
-            }
-            attr_set[which][1] = smem;
-        }
-    }
     cudaError_t e = cudaMemsetAsync(x, 0, (size_t)g.V * 24 * sizeof(R), st);
     if (e != cudaSuccess) return e;
     const int nblocks = sg.nblk[0] * sg.nblk[1] * sg.nblk[2] * sg.nblk[3];
@@ -252,24 +542,21 @@ static cudaError_t sap_t(const Geom &g, const SapGeom &sg, const LT *U, const ST
     // residuals in place and the grid can hold only that colour
     const bool even = !(sg.nblk[0] & 1) && !(sg.nblk[1] & 1) && !(sg.nblk[2] & 1) && !(sg.nblk[3] & 1);
     const int grid = even ? nblocks / 2 : nblocks;
-    const int threads = (sg.nb + 31) / 32 * 32;
+    const R m4 = m0 + (R)4;
     bool x_zero = true;
     for (int cyc = 0; cyc < cycles; cyc++) {
         for (int colour = 0; colour < 2; colour++) {
             if (x_zero) {
-                k_sap_block<R, LT, ST, false><<<grid, threads, smem, st>>>(g, sg, U, v, x, m0 + (R)4, colour,
-                                                                           mr_iters, even);
+                e = launch_blocks<R, LT, ST, false>(g, sg, U, v, x, m4, colour, mr_iters, even, grid, st);
             } else if (even) {
-                k_sap_block<R, LT, ST, true><<<grid, threads, smem, st>>>(g, sg, U, v, x, m0 + (R)4, colour,
-                                                                          mr_iters, even);
+                e = launch_blocks<R, LT, ST, true>(g, sg, U, v, x, m4, colour, mr_iters, even, grid, st);
             } else {
                 // r = v - D_W x on the whole lattice, then the block solves from r
                 if ((e = wil(g, U, x, r, m0, 0, (R)-1, v, (R)1, st)) != cudaSuccess) return e;
-                k_sap_block<R, LT, ST, false><<<grid, threads, smem, st>>>(g, sg, U, r, x, m0 + (R)4, colour,
-                                                                           mr_iters, even);
+                e = launch_blocks<R, LT, ST, false>(g, sg, U, r, x, m4, colour, mr_iters, even, grid, st);
             }
             count_launches(1);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (e != cudaSuccess) return e;
             x_zero = false;
         }
     }

@@ -8,7 +8,8 @@ struct SapGeom {
     int b[4];        // block extent per direction
     int nblk[4];     // blocks per direction
     int stride[4];   // local lexicographic strides inside a block
-    int nb;          // sites per block (threads per CTA)
+    int nb;          // sites per block
+    int tps;         // threads per site of the FP32 block kernel (1, 2 or 4; FP64 uses 1)
 };
 
 inline SapGeom make_sap_geom(const Geom &g, const int b[4]) {
@@ -22,6 +23,7 @@ inline SapGeom make_sap_geom(const Geom &g, const int b[4]) {
     s.stride[1] = b[3] * b[2];
     s.stride[0] = b[3] * b[2] * b[1];
     s.nb = b[0] * b[1] * b[2] * b[3];
+    s.tps = 1;
     return s;
 }
 

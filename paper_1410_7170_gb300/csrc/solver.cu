@@ -273,7 +273,8 @@ static ovl_status wilson_solve(Ctx *c, Krylov<T> &k, const T *in, T *out, double
         ST(c->alloc(&buf, (size_t)c->n64 * sizeof(T)));
         scratch = (T *)buf;
     }
-    const SapGeom sg = make_sap_geom(c->g, c->p.sap_block);
+    SapGeom sg = make_sap_geom(c->g, c->p.sap_block);
+    sg.tps = c->sap_tps;
     auto mv = [&](const T *a, T *o, double) -> ovl_status {
         CK(Ops<T>::wilson(c, a, o, m0));
         return OVL_OK;
@@ -345,6 +346,13 @@ ovl_status wilson_solve_eo(Ctx *c, const double2 *b, double2 *x, double m0, doub
 }
 
 int batch_size_for(Ctx *c, int want);
+// Most accurate sign request the lower-precision multishift serves in the mixed modes:
+// FP32 vectors, FP16-stored directions (11 significant bits, per-site scale), BF16-stored
+// directions (8 significant bits).
+static double low_sign_floor(int precision) {
+    return precision == OVL_MIXED_BF16 ? 1e-2 : precision == OVL_MIXED_HALF ? 1e-3 : 1e-5;
+}
+
 
 ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -400,9 +408,9 @@ ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, 
         ST(c->norm2_d((const double *)c->d_x, &xx));
         // D_N in FP64; in the mixed modes, a relaxed product whose requested accuracy is
         // within reach of the lower-precision multishift (Sec. 5.2 lets it grow as the
-        // residual falls) runs in FP32 (FP16-stored directions in OVL_MIXED_HALF).
+        // residual falls) runs in FP32 (16-bit stored directions in OVL_MIXED_HALF/BF16).
         const bool mixed = c->p.precision != OVL_FP64;
-        const double low_ok = c->p.precision == OVL_MIXED_HALF ? 1e-3 : 1e-5;
+        const double low_ok = low_sign_floor(c->p.precision);
         auto mv = [&](const double *a, double *o, double rel_now) -> ovl_status {
             const double t = rel_now < 0 ? tight : relax_tol(c, tol, rel_now, tight, 1e-1);
             if (mixed && rel_now >= 0 && t >= low_ok) {
@@ -712,7 +720,8 @@ ovl_status wilson_solve_batch(Ctx *c, int nb, const T *in, T *out, double m0, do
         ST(c->alloc(&buf, (size_t)c->n64 * sizeof(T)));
         scratch = (T *)buf;
     }
-    const SapGeom sg = make_sap_geom(c->g, c->p.sap_block);
+    SapGeom sg = make_sap_geom(c->g, c->p.sap_block);
+    sg.tps = c->sap_tps;
     const long n = c->n64;
     auto mv = [&](const T *a, T *o, const double *) -> ovl_status {
         if (sizeof(T) == 8)
@@ -785,7 +794,7 @@ ovl_status solve_batch(Ctx *c, double2 *x, const double2 *b, int nb, double tol,
         fb = c->fbat + (long)nb * n;
     }
     const double tight = std::max(1e-14, std::min(c->p.sign_tol, 0.1 * tol));
-    const double low_ok = c->p.precision == OVL_MIXED_HALF ? 1e-3 : 1e-5;
+    const double low_ok = low_sign_floor(c->p.precision);
     // inner batched FP32 FGMRES on D_N, preconditioned by the batched Wilson solve
     auto inner = [&](const float *in, float *out, const char *act) -> ovl_status {
         ST(ensure_krylov_batch<float>(c, c->kbo_inner, c->kb_n[1], std::min(c->p.restart_inner, 32), nb));

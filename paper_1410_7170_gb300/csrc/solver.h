@@ -110,6 +110,9 @@ struct Ctx {
     long stat_ms64 = 0, stat_ms32 = 0, stat_prec = 0;
     int stat_inner = 0;
     float tune_ms[4] = {0, 0, 0, 0};   // stencil ms: fp64 1/4 tps, fp32 1/4 tps
+    int sap_tps = 1;                   // threads per site of the FP32 Schwarz block kernel
+    bool sap_tuned = false;
+    float sap_ms[3] = {0, 0, 0};       // one FP32 Schwarz cycle, ms: 1, 2, 4 threads per site
 
     ~Ctx();
     ovl_status alloc(void **p, size_t bytes);
@@ -139,6 +142,7 @@ struct Ctx {
     ovl_status sigma_min_estimate(double *smin);
     ovl_status set_zolotarev();
     ovl_status autotune();
+    ovl_status autotune_sap();
 };
 
 ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats);

@@ -149,6 +149,40 @@ __device__ __forceinline__ void acc_bwd(int mu, cpx<R> acc[12], const cpx<R> a0[
     }
 }
 
+// The two hops of direction MU at site (p, i) with coordinates x, added into acc
+// (First: acc is empty and the forward hop assigns it).
+template <int MU, bool First, typename R, typename LT, typename ST>
+__device__ __forceinline__ void hop_dir(const Geom &g, const LT *__restrict__ U, ST in, int p, int i, const int x[4],
+                                        cpx<R> acc[12]) {
+    const int q = 1 - p;
+    {   // forward neighbour x + mu, link U_mu(x) stored at (p, i)
+        int y[4] = {x[0], x[1], x[2], x[3]};
+        y[MU] = (x[MU] + 1 == g.L[MU]) ? 0 : x[MU] + 1;
+        const int j = eo_index(g, y);
+        cpx<R> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
+        load_spinor<R>(in, g.Vh, q, j, s);
+        load_link<R>(U, g.Vh, p, MU, i, u);
+        proj_fwd(MU, s, h0, h1);
+        if (MU == 0) flip_half(h0, h1, g.antiperiodic && x[0] == g.L[0] - 1);
+        su3_mul(u, h0, a0);
+        su3_mul(u, h1, a1);
+        acc_fwd<First>(MU, acc, a0, a1);
+    }
+    {   // backward neighbour x - mu, link U_mu(x - mu)^H stored at (q, j)
+        int y[4] = {x[0], x[1], x[2], x[3]};
+        y[MU] = (x[MU] == 0) ? g.L[MU] - 1 : x[MU] - 1;
+        const int j = eo_index(g, y);
+        cpx<R> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
+        load_spinor<R>(in, g.Vh, q, j, s);
+        load_link<R>(U, g.Vh, q, MU, j, u);
+        proj_bwd(MU, s, h0, h1);
+        if (MU == 0) flip_half(h0, h1, g.antiperiodic && x[0] == 0);
+        su3_dag_mul(u, h0, a0);
+        su3_dag_mul(u, h1, a1);
+        acc_bwd(MU, acc, a0, a1);
+    }
+}
+
 // Hopping sum H(x) = sum_mu [(1-g_mu) U_mu(x) in(x+mu) + (1+g_mu) U_mu(x-mu)^H in(x-mu)]
 // for the site (p, i); `in` is any spinor storage accepted by load_spinor.
 template <typename R, typename LT, typename ST>
@@ -156,37 +190,10 @@ __device__ __forceinline__ void wilson_hop(const Geom &g, const LT *__restrict__
                                            cpx<R> acc[12]) {
     int x[4];
     eo_coords(g, p, i, x);
-    const int q = 1 - p;
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        {   // forward neighbour x + mu, link U_mu(x) stored at (p, i)
-            int y[4] = {x[0], x[1], x[2], x[3]};
-            y[mu] = (x[mu] + 1 == g.L[mu]) ? 0 : x[mu] + 1;
-            const int j = eo_index(g, y);
-            cpx<R> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
-            load_spinor<R>(in, g.Vh, q, j, s);
-            load_link<R>(U, g.Vh, p, mu, i, u);
-            proj_fwd(mu, s, h0, h1);
-            if (mu == 0) flip_half(h0, h1, g.antiperiodic && x[0] == g.L[0] - 1);
-            su3_mul(u, h0, a0);
-            su3_mul(u, h1, a1);
-            if (mu == 0) acc_fwd<true>(mu, acc, a0, a1);
-            else acc_fwd<false>(mu, acc, a0, a1);
-        }
-        {   // backward neighbour x - mu, link U_mu(x - mu)^H stored at (q, j)
-            int y[4] = {x[0], x[1], x[2], x[3]};
-            y[mu] = (x[mu] == 0) ? g.L[mu] - 1 : x[mu] - 1;
-            const int j = eo_index(g, y);
-            cpx<R> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
-            load_spinor<R>(in, g.Vh, q, j, s);
-            load_link<R>(U, g.Vh, q, mu, j, u);
-            proj_bwd(mu, s, h0, h1);
-            if (mu == 0) flip_half(h0, h1, g.antiperiodic && x[0] == 0);
-            su3_dag_mul(u, h0, a0);
-            su3_dag_mul(u, h1, a1);
-            acc_bwd(mu, acc, a0, a1);
-        }
-    }
+    hop_dir<0, true, R>(g, U, in, p, i, x, acc);
+    hop_dir<1, false, R>(g, U, in, p, i, x, acc);
+    hop_dir<2, false, R>(g, U, in, p, i, x, acc);
+    hop_dir<3, false, R>(g, U, in, p, i, x, acc);
 }
 
 // res = (m0+4) own - 1/2 hop

@@ -182,6 +182,7 @@ def test_gmres_solve_matches_dense_lu(c1):
     (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_FP32, 1),
     (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_FP32, 4),
     (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_HALF, 1),
+    (ovl.OVL_PREC_RECURSIVE, ovl.OVL_MIXED_BF16, 1),
 ])
 def test_preconditioned_solves_match_dense_lu(c1, precond, precision, tps):
     dims, U, rho, DN, S, aw = c1
@@ -258,6 +259,37 @@ def test_wilson_solve_residual_and_sap_quality(precision, tol):
     assert its[1] < its[0]
 
 
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (12, 8, 8, 8)])
+def test_sap_threads_per_site_variants_agree(dims):
+    """The FP32 Schwarz block kernel with 1, 2 or 4 threads per site computes the same
+    smoother up to FP32 rounding (only the order of the hop sums differs). One FGMRES step
+    (tol 0.9) returns a multiple of the smoother's output, so the solutions are compared
+    directly; each variant then also solves to 1e-4 (checked with the oracle's D_W) in about the
+    same number of iterations. With
+    12 x 8^3 the blocks per direction are odd in x0, which takes the path that forms the
+    residual on the whole lattice before the block solves."""
+    U = synth.gauge_field(dims, 0.5, 1203, stout_steps=3)
+    b = synth.rhs_gaussian(dims, 2203)
+    m0 = -0.3
+    one, its, res = {}, {}, {}
+    for tps in (1, 2, 4):
+        op = ovl.Overlap(U, dims, 1.0, 0.01, params(precision=ovl.OVL_MIXED_FP32, sap_tps=tps,
+                                                    prec_max_iter=400, prec_restart=32))
+        assert op.tuning_sap()["sap_tps"] == tps
+        x = np.zeros_like(b)
+        assert op.wilson_solve(x, b, m0, 0.9) in (1, 2)
+        one[tps] = x
+        x = np.zeros_like(b)
+        its[tps] = op.wilson_solve(x, b, m0, 1e-4)
+        r = b - sparse.wilson(x, U, dims, m0)
+        res[tps] = np.linalg.norm(r) / np.linalg.norm(b)
+        op.close()
+    for tps in (2, 4):
+        assert relmax(one[tps], one[1]) < 1e-5, (tps, relmax(one[tps], one[1]))
+        assert abs(its[tps] - its[1]) <= 2, its
+    assert max(res.values()) < 1.5e-4, res
+
+
 def test_autotuner_reports_a_choice():
     dims = (16, 16, 16, 16)
     U = synth.gauge_field(dims, 0.5, 7, stout_steps=0)
@@ -265,6 +297,11 @@ def test_autotuner_reports_a_choice():
     t = op.tuning()
     assert t["tps64"] in (1, 4) and t["tps32"] in (1, 4)
     assert all(m > 0 for m in t["ms"])
+    op.close()
+    op = ovl.Overlap(U, dims, 1.0, 0.01, params(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32))
+    t = op.tuning_sap()
+    assert t["sap_tps"] in (1, 2, 4) and all(m > 0 for m in t["ms"])
+    assert t["ms"][(1, 2, 4).index(t["sap_tps"])] == min(t["ms"])
     op.close()
 
 
@@ -277,6 +314,25 @@ def test_config4_half_storage_full_size():
     b = torch.from_numpy(synth.rhs_z2(dims, 2004)).cuda()
     op = ovl.Overlap(U, dims, 1.0, 0.01, ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE,
                                                             precision=ovl.OVL_MIXED_HALF))
+    x = torch.zeros_like(b)
+    st, stats = op.ovl_solve(x, b, 1, 1e-10)
+    r = torch.empty_like(b)
+    op.ovl_apply(r, x, 1e-13)
+    res = ((b - r).norm() / b.norm()).item()
+    assert res < 2e-10, (res, stats)
+    assert stats["ms_iters_low"] > 0
+    op.close()
+
+
+@pytest.mark.parametrize("precision", [ovl.OVL_MIXED_FP32, ovl.OVL_MIXED_HALF, ovl.OVL_MIXED_BF16])
+def test_16bit_storage_solves_16x16x16x16(precision):
+    """16^4, 3-stout links, mu = 0.01: the recursive solver with FP32, FP16-stored and
+    BF16-stored inner multishift directions reaches tol 1e-10 in the true FP64 residual,
+    and the 16-bit modes use their lower-precision sign."""
+    dims = (16, 16, 16, 16)
+    U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1002, stout_steps=3)).cuda()
+    b = torch.from_numpy(synth.rhs_gaussian(dims, 2002)).cuda()
+    op = ovl.Overlap(U, dims, 1.0, 0.01, ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=precision))
     x = torch.zeros_like(b)
     st, stats = op.ovl_solve(x, b, 1, 1e-10)
     r = torch.empty_like(b)
