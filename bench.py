@@ -225,18 +225,24 @@ def run_ours(args, rank, world, dist):
     pk, pk_kind = peaks()
     # dominant kernel of the timed region (library event timings, same launches as the work)
     kern = {k: prof[k] for k in ("ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_f32")}
-    dom = max(kern, key=lambda k: kern[k]["ms"])
+    V = int(np.prod(DIMS))
+    for name, v in kern.items():
+        # the library times one iteration of every queued chunk: per-launch averages from the
+        # timed launches, class totals extrapolated to all launches
+        v["avg_ms"] = v["ms"] / v["timed"] if v["timed"] else 0.0
+        v["total_ms"] = v["avg_ms"] * v["launches"]
+        v["timed_flops"] = 1368.0 * V * v["timed"] if name.startswith("ms_stencil") else 0.0
+    dom = max(kern, key=lambda k: kern[k]["total_ms"])
     kd = kern[dom]
     n_l = kd["launches"]
     if dom == "ms_stencil_f64":
         # FP64 stencil: bound by the FP64 pipes (1368 flop and 768 B per site: 1.8 flop/B)
-        achieved = kd["flops"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
+        achieved = kd["timed_flops"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
         peak, unit, bound, pkind = FP64_PEAK_GFLOPS, "GFLOP/s", "alu", "nominal FP64 rate (recipe table)"
     else:
-        achieved = kd["bytes"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
+        achieved = kd["timed_bytes"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
         peak, unit, bound, pkind = pk["hbm_gbs"], "GB/s", "hbm", pk_kind
     per_launch_bytes = kd["bytes"] / n_l if n_l else None
-    V = int(np.prod(DIMS))
     spinor_bytes = V * 12 * 16
     out = {
         "metric": METRIC,
@@ -268,14 +274,16 @@ def run_ours(args, rank, world, dist):
         "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": (achieved / peak) if achieved else None, "peak_kind": pkind,
                      "traffic": traffic_from_profiles(dom), "algorithmic_bytes_per_launch": per_launch_bytes,
-                     "launches": n_l, "avg_launch_us": (kd["ms"] / n_l * 1e3) if n_l else None,
-                     "kernels": {k: {"ms": v["ms"], "launches": v["launches"],
-                                     "share": v["ms"] / max(1e-30, sum(x["ms"] for x in kern.values())),
-                                     "GB/s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
-                                     "GFLOP/s": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                     "launches": n_l, "timed_launches": kd["timed"], "avg_launch_us": kd["avg_ms"] * 1e3,
+                     "kernels": {k: {"total_ms": v["total_ms"], "launches": v["launches"], "timed": v["timed"],
+                                     "avg_us": v["avg_ms"] * 1e3,
+                                     "share": v["total_ms"] / max(1e-30, sum(x["total_ms"] for x in kern.values())),
+                                     "GB/s": (v["timed_bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
+                                     "GFLOP/s": (v["timed_flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                                  for k, v in kern.items()},
                      "hbm_peak_gbs": pk["hbm_gbs"],
-                     "timing": "CUDA events recorded by the library around each launch in the timed region"},
+                     "timing": "CUDA events recorded by the library around the kernels of one multishift "
+                               "iteration of every queued chunk of 8, inside the timed region"},
         "e2e": {"value": e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * spinor_bytes,
                 "d2h_bytes_per_step": spinor_bytes},
         "gpu_launches": prof["launches"],

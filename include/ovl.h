@@ -77,7 +77,7 @@ typedef struct {
     int restart;            /* (F)GMRES restart length m (Table 2: 100) */
     int relax;              /* 1: sign accuracy relaxed to tol_outer/||r_k||_rel * relax_factor (Sec. 5.2) */
     double relax_factor;    /* Table 2: 1e-2 */
-    int n_poles;            /* Zolotarev poles n (1..64; default 20) */
+    int n_poles;            /* Zolotarev poles n, the largest degree used (1..64; default 20) */
     double lambda_min;      /* spectral interval of |Q|; 0 = estimate by Lanczos at ovl_create */
     double lambda_max;
     double sign_tol;        /* accuracy of sign_apply inside ovl_apply/ovl_solve when relax = 0 */
@@ -101,6 +101,9 @@ typedef struct {
     int check_every;        /* multishift iterations between host convergence checks */
     int stencil_tps;        /* threads per lattice site of the stencils: 0 = autotune, 1 or 4 = forced */
     int sap_tps;            /* threads per block site of the FP32 Schwarz block solves: 0 = autotune, 1, 2 or 4 */
+    int adaptive_poles;     /* 1 (default): each sign application uses the smallest Zolotarev degree
+                               n <= n_poles whose uniform error delta(k, n) is <= 1/10 of its requested
+                               accuracy; 0: always n_poles */
 } ovl_params;
 
 /* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
@@ -112,6 +115,12 @@ typedef struct {
     long prec_iters;        /* Wilson FGMRES iterations inside the preconditioner */
     double true_rel_resid;  /* max over RHS of ||b - D_N x|| / ||b||, recomputed in FP64 at exit */
     double seconds;         /* wall time of the call */
+    double t_sign_fp64;     /* wall time inside FP64 sign applications (single-RHS path) */
+    double t_sign_low;      /* wall time inside FP32/FP16/BF16 sign applications (single-RHS path) */
+    double t_prec;          /* wall time inside inexact Wilson solves (single-RHS path); the rest
+                               of `seconds` is (F)GMRES orthogonalisation and host work. The phase
+                               times are exact (stream synchronised at each phase end) only while
+                               ovl_prof_enable is on. */
 } ovl_stats;
 
 /* Fills *p with the defaults. Returns OVL_EINVAL if p is NULL. */
@@ -187,17 +196,21 @@ ovl_status ovl_info(const ovl_ctx *ctx, double *lambda_min, double *lambda_max, 
 ovl_status ovl_zolotarev(double k, int n, double *d0, double *a, double *c, double *delta);
 
 /* Instrumentation of the running library (used by the benchmark; not part of the
- * paper's method). With profiling enabled, the multishift CG records CUDA events
- * around its stencil and shift-update kernels in the same queued work (event nodes
- * inside the captured graphs) and logs the shifts each iteration updated, so that
- * kernel durations and algorithmic bytes (reals per site: Q p 96, residual update
- * 144, shift update 72 + 48 per updated shift) are accumulated from the launches
- * that do the work. Timings cost one event pair per kernel. */
+ * paper's method). With profiling enabled, the multishift CG records CUDA events around
+ * the three kernels of one iteration of every queued chunk of check_every iterations
+ * (the middle one; event nodes inside the captured graphs), a sample that keeps the
+ * event nodes from slowing the other iterations, and logs the shifts each iteration
+ * updated, so that algorithmic bytes (reals per site: Q p 96, residual update 144, shift
+ * update 72 + 48 per updated shift) are known for every launch. The achieved rate of a
+ * class is timed_bytes / ms (or timed flops / ms); its total time is estimated as
+ * ms / timed * launches. */
 typedef struct {
-    double ms;              /* summed event time of the kernel class */
-    long launches;
-    double bytes;           /* summed algorithmic bytes */
-    double flops;           /* summed algorithmic flops (stencils: 1368 per site) */
+    double ms;              /* summed event time of the timed launches of the class */
+    long launches;          /* all launches of the class */
+    double bytes;           /* algorithmic bytes of all launches */
+    double flops;           /* algorithmic flops of all launches (stencils: 1368 per site) */
+    long timed;             /* launches that were timed */
+    double timed_bytes;     /* algorithmic bytes of the timed launches */
 } ovl_prof_kernel;
 
 typedef struct {

@@ -40,7 +40,7 @@ class ovl_params(ctypes.Structure):
         ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_iters", ctypes.c_int),
         ("prec_restart", ctypes.c_int), ("prec_max_iter", ctypes.c_int), ("rhs_block", ctypes.c_int),
         ("use_graphs", ctypes.c_int), ("check_every", ctypes.c_int), ("stencil_tps", ctypes.c_int),
-        ("sap_tps", ctypes.c_int),
+        ("sap_tps", ctypes.c_int), ("adaptive_poles", ctypes.c_int),
     ]
 
 
@@ -48,7 +48,8 @@ class ovl_stats(ctypes.Structure):
     _fields_ = [
         ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("ms_iters_fp64", ctypes.c_long),
         ("ms_iters_low", ctypes.c_long), ("prec_iters", ctypes.c_long), ("true_rel_resid", ctypes.c_double),
-        ("seconds", ctypes.c_double),
+        ("seconds", ctypes.c_double), ("t_sign_fp64", ctypes.c_double), ("t_sign_low", ctypes.c_double),
+        ("t_prec", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -75,7 +76,7 @@ class ovl_result(ctypes.Structure):
 
 class ovl_prof_kernel(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_long), ("bytes", ctypes.c_double),
-                ("flops", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("timed", ctypes.c_long), ("timed_bytes", ctypes.c_double)]
 
 
 PROF_KERNELS = ["ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_f32"]
@@ -87,7 +88,8 @@ class ovl_prof(ctypes.Structure):
     def as_dict(self):
         d = {"launches": self.launches, "valid": self.valid}
         for name, k in zip(PROF_KERNELS, self.k):
-            d[name] = {"ms": k.ms, "launches": k.launches, "bytes": k.bytes, "flops": k.flops}
+            d[name] = {"ms": k.ms, "launches": k.launches, "bytes": k.bytes, "flops": k.flops,
+                       "timed": k.timed, "timed_bytes": k.timed_bytes}
         return d
 
 

@@ -60,6 +60,7 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->check_every = 8;
     p->stencil_tps = 0;
     p->sap_tps = 0;
+    p->adaptive_poles = 1;
     return OVL_OK;
 }
 
@@ -84,6 +85,7 @@ static ovl_status validate_params(const ovl_params &p, const int L[4], std::stri
     if (p.rhs_block < 1 || p.rhs_block > 12) { err = "rhs_block must be in [1,12]"; return OVL_EINVAL; }
     if (p.stencil_tps != 0 && p.stencil_tps != 1 && p.stencil_tps != 4) { err = "stencil_tps must be 0, 1 or 4"; return OVL_EINVAL; }
     if (p.sap_tps != 0 && p.sap_tps != 1 && p.sap_tps != 2 && p.sap_tps != 4) { err = "sap_tps must be 0, 1, 2 or 4"; return OVL_EINVAL; }
+    if (p.adaptive_poles != 0 && p.adaptive_poles != 1) { err = "adaptive_poles must be 0 or 1"; return OVL_EINVAL; }
     for (int m = 0; m < 4 && p.precond != OVL_PREC_NONE; m++) {
         if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m]) {
             err = "sap_block must be even and divide the lattice extent";
@@ -143,7 +145,7 @@ Ctx::~Ctx() {
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
     for (int w = 0; w < 2; w++)
         if (ev_ready[w])
-            for (int k = 0; k < kMaxChunk * 4; k++) cudaEventDestroy(ev[w][k]);
+            for (int k = 0; k < 4; k++) cudaEventDestroy(ev[w][k]);
     for (void *p : allocs) cudaFree(p);
     if (h_pinned) cudaFreeHost(h_pinned);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -212,27 +214,47 @@ ovl_status Ctx::export_vec(const double2 *src, double *dst) {
 }
 
 // ------------------------------------------------------------------ multishift sign
-// Fills the multishift state for tolerance tol and uploads it.
-ovl_status Ctx::ms_setup(MsState *d_state, double tol) {
-    Ctx *c = this;
-    MsState &s = *h_ms;
+// Zolotarev degree for a sign application of relative accuracy tol: the smallest n <=
+// n_poles whose uniform approximation error delta(k, n) is at most tol / 10, so that the
+// rational approximation stays an order below the multishift CG's own error (with
+// adaptive_poles = 0: always n_poles). Fewer poles mean fewer shifted directions to
+// update and a larger smallest shift (faster CG convergence).
+int Ctx::pick_poles(double tol) const {
+    if (!p.adaptive_poles) return npole;
+    for (int n = 1; n < npole; n++)
+        if (zs_delta[n - 1] <= 0.1 * tol) return n;
+    return npole;
+}
+
+// Multishift state of degree n for tolerance tol.
+void Ctx::fill_poles(MsState &s, int n, double tol) const {
     memset(&s, 0, sizeof(MsState));
-    s.n = npole;
+    s.n = n;
     s.tol = tol;
     s.alpha_prev = 1.0;
     s.beta_prev = 0.0;
-    for (int l = 0; l < npole; l++) {
-        s.sigma[l] = lam_min * lam_min * zc[l];
-        s.w[l] = za[l] * lam_min * lam_min;
+    const std::vector<double> &a = zs_a[n - 1], &c = zs_c[n - 1];
+    const double d0 = zs_d0[n - 1];
+    for (int l = 0; l < n; l++) {
+        s.sigma[l] = lam_min * lam_min * c[l];
+        s.w[l] = a[l] * lam_min * lam_min;
         // ||(d0/lmin) Q w_l (Q^2+sigma_l)^{-1} r_l|| <= d0 |a_l| ||r_l|| / (2 sqrt(c_l)); summed over l
-        s.crit[l] = npole * zd0 * fabs(za[l]) / (2.0 * sqrt(zc[l]));
+        s.crit[l] = n * d0 * fabs(a[l]) / (2.0 * sqrt(c[l]));
         s.zeta[l] = 1.0;
         s.zeta_prev[l] = 1.0;
         s.active[l] = 1;
     }
-    s.hist = prof ? d_hist : nullptr;
-    s.hist_cap = prof ? hist_cap : 0;
+}
+
+// Fills the multishift state for tolerance tol and uploads it; *n_out = the degree used.
+ovl_status Ctx::ms_setup(MsState *d_state, double tol, int *n_out) {
+    Ctx *c = this;
+    const int n = pick_poles(tol);
+    fill_poles(*h_ms, n, tol);
+    h_ms->hist = prof ? d_hist : nullptr;
+    h_ms->hist_cap = prof ? hist_cap : 0;
     CK(cudaMemcpyAsync(d_state, h_ms, sizeof(MsState), cudaMemcpyHostToDevice, stream));
+    *n_out = n;
     return OVL_OK;
 }
 
@@ -245,11 +267,12 @@ template <typename Iter>
 ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes, Iter iter_fn, int *iters_out) {
     Ctx *c = this;
     const int chunk = std::min(p.check_every, kMaxChunk);
+    const int sample = chunk / 2;   // the iteration of every chunk whose kernels are timed
     const double rbytes = which == 0 ? 8.0 : 4.0;
     int done_iters = 0, iter_before = 0;
     GraphSlot &gs = graphs[slot];
     if (prof && !ev_ready[which]) {
-        for (int k = 0; k < kMaxChunk * 4; k++) CK(cudaEventCreate(&ev[which][k]));
+        for (int k = 0; k < 4; k++) CK(cudaEventCreate(&ev[which][k]));
         ev_ready[which] = true;
     }
     if (gs.exec && (gs.chunk != chunk || gs.prof != prof)) {
@@ -264,7 +287,7 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes
                 CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
                 cudaError_t ce = cudaSuccess;
                 for (int k = 0; k < chunk && ce == cudaSuccess; k++)
-                    ce = iter_fn(prof ? &ev[which][4 * k] : nullptr, cudaEventRecordExternal);
+                    ce = iter_fn(prof && k == sample ? ev[which] : nullptr, cudaEventRecordExternal);
                 cudaError_t ee = cudaStreamEndCapture(stream, &graph);
                 set_launch_counting(true);
                 CK(ce);
@@ -278,7 +301,7 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes
             CK(cudaGraphLaunch(gs.exec, stream));
             count_launches(3L * chunk);
         } else {
-            for (int k = 0; k < chunk; k++) CK(iter_fn(prof ? &ev[which][4 * k] : nullptr, 0u));
+            for (int k = 0; k < chunk; k++) CK(iter_fn(prof && k == sample ? ev[which] : nullptr, 0u));
         }
         done_iters += chunk;
         CK(cudaMemcpyAsync(h_ms_small, d_state, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -289,23 +312,28 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes
         if (prof) {
             const int ran = std::min(chunk, iter - iter_before);
             const double V = (double)g.V;
+            ProfAcc &pa = pacc[which];
+            // algorithmic reals per site: Q p: p, 4 links x 12, t; residual: t, links, p, r in/out;
+            // shifts: r, y in/out, each updated p_l in/out
+            const double qb = 96.0 * V * rbytes, rb = 144.0 * V * rbytes;
             for (int k = 0; k < ran; k++) {
+                const double sb = (72.0 * rbytes + shift_bytes * h_hist[k]) * V;
+                pa.n++;
+                pa.q_bytes += qb;
+                pa.r_bytes += rb;
+                pa.s_bytes += sb;
+                if (k != sample) continue;
                 float a = 0, b = 0, d = 0;
-                if (cudaEventElapsedTime(&a, ev[which][4 * k], ev[which][4 * k + 1]) != cudaSuccess ||
-                    cudaEventElapsedTime(&b, ev[which][4 * k + 1], ev[which][4 * k + 2]) != cudaSuccess ||
-                    cudaEventElapsedTime(&d, ev[which][4 * k + 2], ev[which][4 * k + 3]) != cudaSuccess) {
+                if (cudaEventElapsedTime(&a, ev[which][0], ev[which][1]) != cudaSuccess ||
+                    cudaEventElapsedTime(&b, ev[which][1], ev[which][2]) != cudaSuccess ||
+                    cudaEventElapsedTime(&d, ev[which][2], ev[which][3]) != cudaSuccess) {
                     cudaGetLastError();
-                    pacc[which].valid = false;
+                    pa.valid = false;
                     continue;
                 }
-                ProfAcc &pa = pacc[which];
                 pa.q_ms += a; pa.r_ms += b; pa.s_ms += d;
-                pa.q_n++; pa.r_n++; pa.s_n++;
-                // algorithmic reals per site: Q p: p, 4 links x 12, t; residual: t, links, p, r in/out;
-                // shifts: r, y in/out, each updated p_l in/out
-                pa.q_bytes += 96.0 * V * rbytes;
-                pa.r_bytes += 144.0 * V * rbytes;
-                pa.s_bytes += (72.0 * rbytes + shift_bytes * h_hist[k]) * V;
+                pa.q_t++; pa.r_t++; pa.s_t++;
+                pa.q_tb += qb; pa.r_tb += rb; pa.s_tb += sb;
             }
         }
         iter_before = iter;
@@ -329,15 +357,17 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes
 //   mode 0: out = (d0/lmin) gamma5 D_W y = sign(Q) b
 //   mode 1: out = rho b + (d0/lmin) D_W y   = D_N b
 ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
+    PhaseClock pclk(this, &t_sign64);
     Ctx *c = this;
     ST(ensure_ms64());
-    ST(ms_setup(ms64_state, tol));
-    CK(ms_init_f64(g, npole, ms64_state, ms64, b, rs, stream));
+    int n;
+    ST(ms_setup(ms64_state, tol, &n));
+    CK(ms_init_f64(g, n, ms64_state, ms64, b, rs, stream));
     int iters = 0;
     auto fn = [&](cudaEvent_t *e, unsigned f) { return ms_iter_f64(g, U64, m0_ker, ms64_state, ms64, rs, stream, e, f); };
     ST(ms_run(ms64_state, 0, 0, 48.0 * 8.0, fn, &iters));
     stat_ms64 += iters;
-    const double sc = zd0 / lam_min;
+    const double sc = zs_d0[n - 1] / lam_min;
     if (mode == 0) CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 1, sc, nullptr, 0.0, stream));
     else CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 0, sc, b, rho, stream));
     return OVL_OK;
@@ -345,15 +375,16 @@ ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
 
 // FP32 version for the inner (low-accuracy) D_N: b, out FP32 eo spinors.
 ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
+    PhaseClock pclk(this, &t_sign_low);
     Ctx *c = this;
-    int iters = 0;
+    int iters = 0, n = npole;
     const float4 *y;
     if (p.precision == OVL_MIXED_HALF || p.precision == OVL_MIXED_BF16) {
         // shifted directions stored in 16 bits (per site: 48 B, + 4 B norm for FP16, read and written)
         const bool bf = p.precision == OVL_MIXED_BF16;
         ST(ensure_msh());
-        ST(ms_setup(msh_state, tol));
-        CK(ms_init_half(g, npole, msh_state, msh, b, rs, bf, stream));
+        ST(ms_setup(msh_state, tol, &n));
+        CK(ms_init_half(g, n, msh_state, msh, b, rs, bf, stream));
         auto fn = [&](cudaEvent_t *e, unsigned f) {
             return ms_iter_half(g, U32, (float)m0_ker, msh_state, msh, rs, bf, stream, e, f);
         };
@@ -361,8 +392,8 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
         y = msh.y;
     } else {
         ST(ensure_ms32());
-        ST(ms_setup(ms32_state, tol));
-        CK(ms_init_f32(g, npole, ms32_state, ms32, b, rs, stream));
+        ST(ms_setup(ms32_state, tol, &n));
+        CK(ms_init_f32(g, n, ms32_state, ms32, b, rs, stream));
         auto fn = [&](cudaEvent_t *e, unsigned f) {
             return ms_iter_f32(g, U32, (float)m0_ker, ms32_state, ms32, rs, stream, e, f);
         };
@@ -370,7 +401,7 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
         y = ms32.y;
     }
     stat_ms32 += iters;
-    const float sc = (float)(zd0 / lam_min);
+    const float sc = (float)(zs_d0[n - 1] / lam_min);
     if (mode == 0) CK(wilson_f32(g, U32, y, out, (float)m0_ker, 1, sc, nullptr, 0.f, stream));
     else CK(wilson_f32(g, U32, y, out, (float)m0_ker, 0, sc, b, (float)rho, stream));
     return OVL_OK;
@@ -412,22 +443,11 @@ ovl_status Ctx::ensure_batch() {
 // Lock-step multishift solves of nrhs right-hand sides (tolerance tol[y] each); the
 // host polls the first four words (n, iter, done, status) of every state per chunk.
 template <typename ST, typename Init, typename Iter>
-ovl_status Ctx::msb_run(int nrhs, const double *tol, int slot, Init init_fn, Iter iter_fn, long *iters_out) {
+ovl_status Ctx::msb_run(int nrhs, const double *tol, int n, int slot, Init init_fn, Iter iter_fn, long *iters_out) {
     Ctx *c = this;
     for (int y = 0; y < nrhs; y++) {
         MsState &s = h_msb[y];
-        memset(&s, 0, sizeof(MsState));
-        s.n = npole;
-        s.tol = tol[y];
-        s.alpha_prev = 1.0;
-        for (int l = 0; l < npole; l++) {
-            s.sigma[l] = lam_min * lam_min * zc[l];
-            s.w[l] = za[l] * lam_min * lam_min;
-            s.crit[l] = npole * zd0 * fabs(za[l]) / (2.0 * sqrt(zc[l]));
-            s.zeta[l] = 1.0;
-            s.zeta_prev[l] = 1.0;
-            s.active[l] = 1;
-        }
+        fill_poles(s, n, tol[y] > 0 ? tol[y] : 1.0);
         if (!(tol[y] > 0)) s.done = 1;   // a right-hand side that needs no work this time
     }
     CK(cudaMemcpyAsync(msb_state, h_msb, sizeof(MsState) * nrhs, cudaMemcpyHostToDevice, stream));
@@ -489,6 +509,15 @@ ovl_status Ctx::msb_run(int nrhs, const double *tol, int slot, Init init_fn, Ite
     }
 }
 
+// Smallest positive tolerance of a batch (the most demanding right-hand side sets the
+// Zolotarev degree of the whole batch); 1 if none is positive.
+static double min_positive(const double *tol, int n) {
+    double m = 1.0;
+    for (int y = 0; y < n; y++)
+        if (tol[y] > 0 && tol[y] < m) m = tol[y];
+    return m;
+}
+
 ovl_status Ctx::sign64_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode) {
     Ctx *c = this;
     ST(ensure_batch());
@@ -511,9 +540,10 @@ ovl_status Ctx::sign64_batch(const double2 *b, double2 *out, int nrhs, const dou
     long iters = 0;
     auto init = [&]() { return msb_init_f64(g, nrhs, npole, msb_state, msb64, b, rsb, stream); };
     auto it = [&]() { return msb_iter_f64(g, U64, m0_ker, nrhs, npole, msb_state, msb64, rsb, bcounters, stream); };
-    ST((msb_run<double2>(nrhs, tol, 3, init, it, &iters)));
+    const int n = pick_poles(min_positive(tol, nrhs));
+    ST((msb_run<double2>(nrhs, tol, n, 3, init, it, &iters)));
     stat_ms64 += iters * nrhs;
-    const double sc = zd0 / lam_min;
+    const double sc = zs_d0[n - 1] / lam_min;
     CK(wilson_batch_f64(g, U64, msb64.y, out, msb64.stride, nrhs, m0_ker, mode == 0, sc, mode == 1 ? b : nullptr,
                         rho, stream));
     return OVL_OK;
@@ -543,9 +573,10 @@ ovl_status Ctx::sign32_batch(const float4 *b, float4 *out, int nrhs, const doubl
     auto it = [&]() {
         return msb_iter_f32(g, U32, (float)m0_ker, nrhs, npole, msb_state, msb32, rsb, bcounters, stream);
     };
-    ST((msb_run<float4>(nrhs, tol, 4, init, it, &iters)));
+    const int n = pick_poles(min_positive(tol, nrhs));
+    ST((msb_run<float4>(nrhs, tol, n, 4, init, it, &iters)));
     stat_ms32 += iters * nrhs;
-    const float sc = (float)(zd0 / lam_min);
+    const float sc = (float)(zs_d0[n - 1] / lam_min);
     CK(wilson_batch_f32(g, U32, msb32.y, out, msb32.stride, nrhs, (float)m0_ker, mode == 0, sc,
                         mode == 1 ? b : nullptr, (float)rho, stream));
     return OVL_OK;
@@ -860,6 +891,18 @@ ovl_status Ctx::set_zolotarev() {
         err = "Zolotarev coefficients: bad interval";
         return OVL_EINVAL;
     }
+    zs_d0.assign(npole, 0.0);
+    zs_delta.assign(npole, 0.0);
+    zs_a.assign(npole, std::vector<double>());
+    zs_c.assign(npole, std::vector<double>());
+    for (int n = 1; n <= npole; n++) {
+        zs_a[n - 1].assign(n, 0.0);
+        zs_c[n - 1].assign(n, 0.0);
+        if (zolotarev_host(k, n, &zs_d0[n - 1], zs_a[n - 1].data(), zs_c[n - 1].data(), &zs_delta[n - 1]) != 0) {
+            err = "Zolotarev coefficients: bad interval";
+            return OVL_EINVAL;
+        }
+    }
     return OVL_OK;
 }
 
@@ -1117,12 +1160,16 @@ extern "C" ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset) {
         const ProfAcc &pa = c->pacc[w];
         ovl_prof_kernel &st = out->k[2 * w], &sh = out->k[2 * w + 1];
         st.ms = pa.q_ms + pa.r_ms;
-        st.launches = pa.q_n + pa.r_n;
+        st.timed = pa.q_t + pa.r_t;
+        st.launches = 2 * pa.n;
         st.bytes = pa.q_bytes + pa.r_bytes;
+        st.timed_bytes = pa.q_tb + pa.r_tb;
         st.flops = 1368.0 * V * (double)st.launches;
         sh.ms = pa.s_ms;
-        sh.launches = pa.s_n;
+        sh.timed = pa.s_t;
+        sh.launches = pa.n;
         sh.bytes = pa.s_bytes;
+        sh.timed_bytes = pa.s_tb;
         if (!pa.valid) out->valid = 0;
     }
     if (reset) {

@@ -133,7 +133,8 @@ struct MsState {
     double w[kMaxPoles];       // weights of x_l in y
     double crit[kMaxPoles];    // drop shift l when crit_l * |zeta_l| * ||r|| <= tol * ||b||
     double zeta[kMaxPoles], zeta_prev[kMaxPoles];
-    double alpha_l[kMaxPoles], beta_l[kMaxPoles];   // per-shift step sizes for this iteration
+    double alpha_l[kMaxPoles], beta_l[kMaxPoles];   // this iteration's coefficients of the rescaled directions
+                                                    // (y += w_l alpha_l p~_l, p~_l = r + beta_l p~_l)
     int active[kMaxPoles];
     int *hist;                 // optional: hist[k] = shifts updated in iteration k (instrumentation)
     int hist_cap;

@@ -142,8 +142,10 @@ struct ShiftFinB {
                 zn = (den != 0.0) ? zz * zp * ap / den : 0.0;
             }
             const double ratio = (s->zeta[l] != 0.0) ? zn / s->zeta[l] : 0.0;
-            s->alpha_l[l] = a * ratio;
-            s->beta_l[l] = beta * ratio * ratio;
+            // directions stored as p~_l = p_l / zeta_l (see the header): y += w_l a zeta_new p~_l,
+            // p~_l = r + b ratio p~_l
+            s->alpha_l[l] = a * zn;
+            s->beta_l[l] = beta * ratio;
             s->zeta_prev[l] = s->zeta[l];
             s->zeta[l] = zn;
             if (s->crit[l] * fabs(zn) * rnorm <= tolb) s->active[l] = 2;
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(kBlock) k_msb_shifts(MsState *st, int npole, c
                                                        unsigned *counters) {
     using A = typename WordB<ST>::A;
     constexpr int N = WordB<ST>::N;
-    __shared__ A sw[kMaxPoles], sz[kMaxPoles], sb[kMaxPoles];
+    __shared__ A sw[kMaxPoles], sb[kMaxPoles];
     __shared__ int sidx[kMaxPoles];
     __shared__ int sact, sdone;
     const int y = blockIdx.y;
@@ -264,7 +266,6 @@ __global__ void __launch_bounds__(kBlock) k_msb_shifts(MsState *st, int npole, c
                 if (s->active[l]) {
                     sidx[na] = l;
                     sw[na] = (A)(s->w[l] * s->alpha_l[l]);
-                    sz[na] = (A)s->zeta[l];
                     sb[na] = (A)s->beta_l[l];
                     na++;
                 }
@@ -290,11 +291,11 @@ __global__ void __launch_bounds__(kBlock) k_msb_shifts(MsState *st, int npole, c
                 if (a0 + u >= na) break;
                 A pv[N];
                 WordB<ST>::get(w[u], pv);
-                const A wl = sw[a0 + u], zl = sz[a0 + u], bl = sb[a0 + u];
+                const A wl = sw[a0 + u], bl = sb[a0 + u];
 #pragma unroll
                 for (int e = 0; e < N; e++) {
                     yv[e] += wl * pv[e];
-                    pv[e] = zl * rv[e] + bl * pv[e];
+                    pv[e] = rv[e] + bl * pv[e];
                 }
                 Py[(long)sidx[a0 + u] * stride + k] = WordB<ST>::put(pv);
             }

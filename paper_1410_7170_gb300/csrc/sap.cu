@@ -25,43 +25,74 @@ namespace ovl {
 
 namespace {
 
-// Resident CTAs per SM the block kernel is compiled for: FP32 blocks (98 KB of shared
+// Resident CTAs per SM the block kernel is compiled for: FP32 blocks (74 KB of shared
 // memory for 4^4 sites) fit two per SM at 128 registers; FP64 blocks (196 KB) fit one.
 template <typename R> struct SapMinBlocks { static constexpr int value = 2; };
 template <> struct SapMinBlocks<double> { static constexpr int value = 1; };
 
-// Shared-memory layout (R = arithmetic type): spinor s [24][nb], links [4][18][nb].
-template <typename R>
-struct SapSmem {
-    R *s;
-    R *u;
-};
+// Shared-memory copies of a block's spinor and forward links in the word layouts of
+// global memory, one 16-byte load per word: FP32 spinor float4 [6][nb] and links float4
+// [4][3][nb] (rows 0 and 1, row 2 rebuilt in registers), FP64 spinor double2 [12][nb]
+// and links double2 [4][9][nb]. Consecutive threads read consecutive words (no bank
+// conflicts).
+template <typename W> struct SapWords;
+template <> struct SapWords<float4> { static constexpr int spinor = 6, link = 3; };
+template <> struct SapWords<double2> { static constexpr int spinor = 12, link = 9; };
 
-template <typename R>
-__device__ __forceinline__ void sm_load_sp(const R *s, int nb, int t, cpx<R> v[12]) {
+__device__ __forceinline__ void sm_load_sp(const float4 *s, int nb, int t, cpx<float> v[12]) {
 #pragma unroll
-    for (int c = 0; c < 12; c++) v[c] = cpx<R>{s[(2 * c) * nb + t], s[(2 * c + 1) * nb + t]};
-}
-template <typename R>
-__device__ __forceinline__ void sm_store_sp(R *s, int nb, int t, const cpx<R> v[12]) {
-#pragma unroll
-    for (int c = 0; c < 12; c++) {
-        s[(2 * c) * nb + t] = v[c].re;
-        s[(2 * c + 1) * nb + t] = v[c].im;
+    for (int c = 0; c < 6; c++) {
+        const float4 w = s[c * nb + t];
+        v[2 * c] = cpx<float>{w.x, w.y};
+        v[2 * c + 1] = cpx<float>{w.z, w.w};
     }
 }
-template <typename R>
-__device__ __forceinline__ void sm_load_link(const R *u, int nb, int mu, int t, cpx<R> m[3][3]) {
-    const R *b = u + (size_t)mu * 18 * nb + t;
+__device__ __forceinline__ void sm_load_sp(const double2 *s, int nb, int t, cpx<double> v[12]) {
 #pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int c = 0; c < 12; c++) {
+        const double2 w = s[c * nb + t];
+        v[c] = cpx<double>{w.x, w.y};
+    }
+}
+__device__ __forceinline__ void sm_store_sp(float4 *s, int nb, int t, const cpx<float> v[12]) {
 #pragma unroll
-        for (int c = 0; c < 3; c++) m[a][c] = cpx<R>{b[(a * 6 + 2 * c) * nb], b[(a * 6 + 2 * c + 1) * nb]};
+    for (int c = 0; c < 6; c++) s[c * nb + t] = make_float4(v[2 * c].re, v[2 * c].im, v[2 * c + 1].re, v[2 * c + 1].im);
+}
+__device__ __forceinline__ void sm_store_sp(double2 *s, int nb, int t, const cpx<double> v[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; c++) s[c * nb + t] = make_double2(v[c].re, v[c].im);
+}
+__device__ __forceinline__ void sm_load_link(const float4 *u, int nb, int mu, int t, cpx<float> m[3][3]) {
+    const float4 *b = u + mu * 3 * nb + t;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float4 w = b[c * nb];
+        m[(2 * c) / 3][(2 * c) % 3] = cpx<float>{w.x, w.y};
+        m[(2 * c + 1) / 3][(2 * c + 1) % 3] = cpx<float>{w.z, w.w};
+    }
+    reconstruct_row2(m);
+}
+__device__ __forceinline__ void sm_load_link(const double2 *u, int nb, int mu, int t, cpx<double> m[3][3]) {
+    const double2 *b = u + mu * 9 * nb + t;
+#pragma unroll
+    for (int c = 0; c < 9; c++) {
+        const double2 w = b[c * nb];
+        m[c / 3][c % 3] = cpx<double>{w.x, w.y};
+    }
+}
+// The link words of U_mu at (p, i) in global memory, copied to block site t.
+template <typename LT>
+__device__ __forceinline__ void sm_copy_link(LT *u, int nb, int mu, int t, const LT *__restrict__ U, int Vh, int p,
+                                             int i) {
+    constexpr int W = SapWords<LT>::link;
+    const LT *gw = U + ((size_t)(p * 4 + mu) * W) * Vh + i;
+#pragma unroll
+    for (int c = 0; c < W; c++) u[(mu * W + c) * nb + t] = __ldg(gw + (size_t)c * Vh);
 }
 
 // q = D_BB s at local site t (local coords l, extents bx), links of the block in smem.
-template <typename R>
-__device__ __forceinline__ void block_apply(const R *s, const R *u, int nb, int t, const int l[4], const int bx[4],
+template <typename R, typename LT, typename ST>
+__device__ __forceinline__ void block_apply(const ST *s, const LT *u, int nb, int t, const int l[4], const int bx[4],
                                             const int stride[4], R m4, cpx<R> q[12]) {
     cpx<R> acc[12];
 #pragma unroll
@@ -158,8 +189,8 @@ __global__ void __launch_bounds__(kBlock, SapMinBlocks<R>::value) k_sap_block(Ge
         B[0] = rem / sg.nblk[1];
         if (((B[0] + B[1] + B[2] + B[3]) & 1) != colour) return;   // uniform over the CTA
     }
-    R *s = reinterpret_cast<R *>(smem_raw);
-    R *u = s + 24 * nb;
+    ST *s = reinterpret_cast<ST *>(smem_raw);
+    LT *u = reinterpret_cast<LT *>(s + SapWords<ST>::spinor * nb);
     // the CTA is padded to whole warps; threads t >= nb hold no site but join the reductions
     const bool act = threadIdx.x < nb;
     const int t = act ? threadIdx.x : 0;
@@ -174,19 +205,9 @@ __global__ void __launch_bounds__(kBlock, SapMinBlocks<R>::value) k_sap_block(Ge
     const int p = (xg[0] + xg[1] + xg[2] + xg[3]) & 1;
     const int i = eo_index(g, xg);
     // links U_mu(x) of the block sites (forward links; backward ones are the neighbours')
+    if (act)
 #pragma unroll
-    for (int mu = 0; mu < 4 && act; mu++) {
-        cpx<R> m[3][3];
-        load_link<R>(U, g.Vh, p, mu, i, m);
-        R *b = u + (size_t)mu * 18 * nb + t;
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                b[(a * 6 + 2 * c) * nb] = m[a][c].re;
-                b[(a * 6 + 2 * c + 1) * nb] = m[a][c].im;
-            }
-    }
+        for (int mu = 0; mu < 4; mu++) sm_copy_link(u, nb, mu, t, U, g.Vh, p, i);
     cpx<R> res[12], e[12], q[12];
 #pragma unroll
     for (int c = 0; c < 12; c++) {
@@ -208,7 +229,7 @@ __global__ void __launch_bounds__(kBlock, SapMinBlocks<R>::value) k_sap_block(Ge
     for (int it = 0; it < mr_iters; it++) {
         if (act) sm_store_sp(s, nb, t, res);
         __syncthreads();
-        if (act) block_apply<R>(s, u, nb, t, l, sg.b, sg.stride, m4, q);
+        if (act) block_apply<R, LT, ST>(s, u, nb, t, l, sg.b, sg.stride, m4, q);
         R a0 = 0, a1 = 0, a2 = 0;   // per-site and block sums in the arithmetic type
 #pragma unroll
         for (int c = 0; c < 12; c++) {
@@ -242,8 +263,8 @@ __global__ void __launch_bounds__(kBlock, SapMinBlocks<R>::value) k_sap_block(Ge
 // are combined through shared memory, summed over k in a fixed order (deterministic).
 
 // The two block-local hops of direction MU (hops that leave the block are dropped).
-template <int MU, typename R>
-__device__ __forceinline__ void block_hop_dir(const R *s, const R *u, int nb, int t, const int l[4], const int bx[4],
+template <int MU, typename R, typename W>
+__device__ __forceinline__ void block_hop_dir(const W *s, const W *u, int nb, int t, const int l[4], const int bx[4],
                                               const int stride[4], cpx<R> acc[12]) {
     if (l[MU] + 1 < bx[MU]) {
         cpx<R> v[12], h0[3], h1[3], a0[3], a1[3], m[3][3];
@@ -265,25 +286,25 @@ __device__ __forceinline__ void block_hop_dir(const R *s, const R *u, int nb, in
     }
 }
 
-template <int TPS, typename R>
-__device__ __forceinline__ void block_hop_part(int k, const R *s, const R *u, int nb, int t, const int l[4],
+template <int TPS, typename R, typename W>
+__device__ __forceinline__ void block_hop_part(int k, const W *s, const W *u, int nb, int t, const int l[4],
                                                const int bx[4], const int stride[4], cpx<R> acc[12]) {
 #pragma unroll
     for (int c = 0; c < 12; c++) acc[c] = cpx<R>{0, 0};
     if (TPS == 2) {
         if (k == 0) {
-            block_hop_dir<0>(s, u, nb, t, l, bx, stride, acc);
-            block_hop_dir<1>(s, u, nb, t, l, bx, stride, acc);
+            block_hop_dir<0, R>(s, u, nb, t, l, bx, stride, acc);
+            block_hop_dir<1, R>(s, u, nb, t, l, bx, stride, acc);
         } else {
-            block_hop_dir<2>(s, u, nb, t, l, bx, stride, acc);
-            block_hop_dir<3>(s, u, nb, t, l, bx, stride, acc);
+            block_hop_dir<2, R>(s, u, nb, t, l, bx, stride, acc);
+            block_hop_dir<3, R>(s, u, nb, t, l, bx, stride, acc);
         }
     } else {
         switch (k) {
-            case 0: block_hop_dir<0>(s, u, nb, t, l, bx, stride, acc); break;
-            case 1: block_hop_dir<1>(s, u, nb, t, l, bx, stride, acc); break;
-            case 2: block_hop_dir<2>(s, u, nb, t, l, bx, stride, acc); break;
-            default: block_hop_dir<3>(s, u, nb, t, l, bx, stride, acc); break;
+            case 0: block_hop_dir<0, R>(s, u, nb, t, l, bx, stride, acc); break;
+            case 1: block_hop_dir<1, R>(s, u, nb, t, l, bx, stride, acc); break;
+            case 2: block_hop_dir<2, R>(s, u, nb, t, l, bx, stride, acc); break;
+            default: block_hop_dir<3, R>(s, u, nb, t, l, bx, stride, acc); break;
         }
     }
 }
@@ -384,9 +405,9 @@ __global__ void __launch_bounds__(256 * TPS, 1)
         B[0] = rem / sg.nblk[1];
         if (((B[0] + B[1] + B[2] + B[3]) & 1) != colour) return;   // uniform over the CTA
     }
-    R *s = reinterpret_cast<R *>(smem_raw);   // [24][nb] spinor of the block
-    R *u = s + 24 * nb;                        // [4][18][nb] forward links
-    R *X = u + 72 * nb;                        // [TPS][24][nb] partial hopping sums
+    float4 *s = reinterpret_cast<float4 *>(smem_raw);   // [6][nb] spinor of the block
+    float4 *u = s + 6 * nb;                              // [4][3][nb] forward links
+    R *X = reinterpret_cast<R *>(u + 12 * nb);           // [TPS][24][nb] partial hopping sums
     const int k = threadIdx.x / nbp;           // warp-uniform
     const int ts = threadIdx.x - k * nbp;
     const bool act = ts < nb;
@@ -402,22 +423,10 @@ __global__ void __launch_bounds__(256 * TPS, 1)
     for (int mu = 0; mu < 4; mu++) xg[mu] = B[mu] * sg.b[mu] + l[mu];
     const int p = (xg[0] + xg[1] + xg[2] + xg[3]) & 1;
     const int i = eo_index(g, xg);
-    if (act) {   // forward links of this thread's directions
+    if (act)   // forward links of this thread's directions
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            if (mu * TPS / 4 != k) continue;
-            cpx<R> m[3][3];
-            load_link<R>(U, g.Vh, p, mu, i, m);
-            R *b = u + (size_t)mu * 18 * nb + t;
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    b[(a * 6 + 2 * c) * nb] = m[a][c].re;
-                    b[(a * 6 + 2 * c + 1) * nb] = m[a][c].im;
-                }
-        }
-    }
+        for (int mu = 0; mu < 4; mu++)
+            if (mu * TPS / 4 == k) sm_copy_link(u, nb, mu, t, U, g.Vh, p, i);
     cpx<R> res[C], e[C], q[C];
 #pragma unroll
     for (int c = 0; c < C; c++) {
@@ -442,18 +451,15 @@ __global__ void __launch_bounds__(256 * TPS, 1)
         }
     }
     for (int it = 0; it < mr_iters; it++) {
-        if (act) {
-            R *b = s + (size_t)(2 * c0) * nb + t;
+        if (act) {   // own components c into the float4 words: complex c is half c % 2 of word c / 2
+            float2 *s2 = reinterpret_cast<float2 *>(s);
 #pragma unroll
-            for (int c = 0; c < C; c++) {
-                b[(2 * c) * nb] = res[c].re;
-                b[(2 * c + 1) * nb] = res[c].im;
-            }
+            for (int c = 0; c < C; c++) s2[2 * ((c0 + c) / 2 * nb + t) + ((c0 + c) & 1)] = make_float2(res[c].re, res[c].im);
         }
         __syncthreads();
         if (act) {
             cpx<R> acc[12];
-            block_hop_part<TPS>(k, s, u, nb, t, l, sg.b, sg.stride, acc);
+            block_hop_part<TPS, R>(k, s, u, nb, t, l, sg.b, sg.stride, acc);
             scatter_part(X, nb, t, k, acc);
         }
         __syncthreads();
@@ -509,7 +515,7 @@ static cudaError_t launch_blocks(const Geom &g, const SapGeom &sg, const LT *U, 
     if constexpr (sizeof(R) == 4) {
         if (sg.tps == 2 || sg.tps == 4) {
             const int nbp = (sg.nb + 31) / 32 * 32;
-            const size_t smem = (size_t)sg.nb * (24 + 72 + 24 * sg.tps) * sizeof(R);
+            const size_t smem = (size_t)sg.nb * (18 * sizeof(float4) + 24 * sg.tps * sizeof(float));
             cudaError_t e;
             if (sg.tps == 2) {
                 if ((e = grant_smem(k_sap_block_mt<2, RES>, smem, granted[1])) != cudaSuccess) return e;
@@ -521,7 +527,7 @@ static cudaError_t launch_blocks(const Geom &g, const SapGeom &sg, const LT *U, 
             return cudaGetLastError();
         }
     }
-    const size_t smem = (size_t)sg.nb * (24 + 4 * 18) * sizeof(R);
+    const size_t smem = (size_t)sg.nb * (SapWords<ST>::spinor * sizeof(ST) + 4 * SapWords<LT>::link * sizeof(LT));
     cudaError_t e;
     if ((e = grant_smem(k_sap_block<R, LT, ST, RES>, smem, granted[0])) != cudaSuccess) return e;
     const int threads = (sg.nb + 31) / 32 * 32;

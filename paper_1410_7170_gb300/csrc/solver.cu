@@ -266,6 +266,7 @@ static ovl_status fgmres(Ctx *c, Krylov<T> &k, T *x, const T *b, double tol, int
 // FGMRES(prec_restart) on D_W(m0_prec), right-preconditioned by SAP cycles.
 template <typename T>
 static ovl_status wilson_solve(Ctx *c, Krylov<T> &k, const T *in, T *out, double m0, double tol, int *iters = nullptr) {
+    PhaseClock pclk(c, &c->t_prec);
     ST(ensure_krylov<T>(c, k, c->p.prec_restart, true));
     T *&scratch = sizeof(T) == 8 ? (T *&)c->sap_r64 : (T *&)c->sap_r32;
     if (!scratch) {
@@ -358,6 +359,7 @@ ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, 
     const auto t0 = std::chrono::steady_clock::now();
     c->stat_ms64 = c->stat_ms32 = c->stat_prec = 0;
     c->stat_inner = 0;
+    c->t_sign64 = c->t_sign_low = c->t_prec = 0;
     const bool flexible = c->p.precond != OVL_PREC_NONE;
     int outer_total = 0;
     double worst = 0.0;
@@ -446,6 +448,9 @@ ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, 
         stats->prec_iters = c->stat_prec;
         stats->true_rel_resid = worst;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->t_sign_fp64 = c->t_sign64;
+        stats->t_sign_low = c->t_sign_low;
+        stats->t_prec = c->t_prec;
     }
     if (!all_conv) {
         c->err = "ovl_solve: tolerance not reached within max_iter";

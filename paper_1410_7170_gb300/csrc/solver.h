@@ -1,5 +1,6 @@
 // Library context and the host-side solver interfaces (internal).
 #pragma once
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -20,9 +21,11 @@ constexpr int kScal = 8192;   // doubles of scalar staging (device d_scal, pinne
 
 // Event timings of the multishift kernels (instrumentation).
 struct ProfAcc {
-    double q_ms = 0, r_ms = 0, s_ms = 0;
-    long q_n = 0, r_n = 0, s_n = 0;
-    double q_bytes = 0, r_bytes = 0, s_bytes = 0;
+    double q_ms = 0, r_ms = 0, s_ms = 0;           // event time of the timed launches
+    long q_t = 0, r_t = 0, s_t = 0;                // timed launches
+    double q_tb = 0, r_tb = 0, s_tb = 0;           // their algorithmic bytes
+    long n = 0;                                    // iterations (launches of each kernel)
+    double q_bytes = 0, r_bytes = 0, s_bytes = 0;  // algorithmic bytes of all launches
     bool valid = true;
 };
 
@@ -65,6 +68,9 @@ struct Ctx {
     // Zolotarev
     int npole = 0;
     double lam_min = 0, lam_max = 0, zd0 = 0, zdelta = 0;
+    // Zolotarev coefficients of every degree n = 1..npole (index n - 1) on [lam_min, lam_max]
+    std::vector<double> zs_d0, zs_delta;
+    std::vector<std::vector<double>> zs_a, zs_c;
     bool lam_estimated = false;
     std::vector<double> za, zc;
     // multishift
@@ -88,7 +94,7 @@ struct Ctx {
     bool prof = false;
     ProfAcc pacc[2];   // per precision slot (0 FP64, 1 FP32)
     long launch_mark = 0;
-    cudaEvent_t ev[2][kMaxChunk * 4] = {};
+    cudaEvent_t ev[2][4] = {};   // profiling: events around the kernels of one sampled iteration
     bool ev_ready[2] = {false, false};
     int *d_hist = nullptr;
     int hist_cap = 0;
@@ -111,6 +117,7 @@ struct Ctx {
     int stat_inner = 0;
     float tune_ms[4] = {0, 0, 0, 0};   // stencil ms: fp64 1/4 tps, fp32 1/4 tps
     int sap_tps = 1;                   // threads per site of the FP32 Schwarz block kernel
+    double t_sign64 = 0, t_sign_low = 0, t_prec = 0;   // phase wall times of the current solve (s)
     bool sap_tuned = false;
     float sap_ms[3] = {0, 0, 0};       // one FP32 Schwarz cycle, ms: 1, 2, 4 threads per site
 
@@ -122,7 +129,9 @@ struct Ctx {
     ovl_status norm2_f(const float *x, double *out);
     ovl_status import_vec(const double *src, double2 *dst);
     ovl_status export_vec(const double2 *src, double *dst);
-    ovl_status ms_setup(MsState *d_state, double tol);
+    int pick_poles(double tol) const;
+    void fill_poles(MsState &s, int n, double tol) const;
+    ovl_status ms_setup(MsState *d_state, double tol, int *n_out);
     // which: instrumentation class (0 FP64, 1 FP32/FP16); slot: CUDA-graph slot;
     // shift_bytes: algorithmic bytes per site of one shift update (read + write of p_l)
     template <typename Iter>
@@ -137,12 +146,25 @@ struct Ctx {
     ovl_status sign64_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode);
     ovl_status sign32_batch(const float4 *b, float4 *out, int nrhs, const double *tol, int mode);
     template <typename ST, typename Init, typename Iter>
-    ovl_status msb_run(int nrhs, const double *tol, int slot, Init init_fn, Iter iter_fn, long *iters_out);
+    ovl_status msb_run(int nrhs, const double *tol, int n, int slot, Init init_fn, Iter iter_fn, long *iters_out);
     ovl_status lanczos_bounds(double *lmin, double *lmax);
     ovl_status sigma_min_estimate(double *smin);
     ovl_status set_zolotarev();
     ovl_status autotune();
     ovl_status autotune_sap();
+};
+
+// Wall time of a solver phase, added to *acc when the scope ends. With profiling on, the
+// context's stream is synchronised first, so that the phase's last kernels are counted.
+struct PhaseClock {
+    Ctx *c;
+    double *acc;
+    std::chrono::steady_clock::time_point t0;
+    PhaseClock(Ctx *c_, double *a) : c(c_), acc(a), t0(std::chrono::steady_clock::now()) {}
+    ~PhaseClock() {
+        if (c->prof) cudaStreamSynchronize(c->stream);
+        *acc += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
 };
 
 ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats);

@@ -2,11 +2,12 @@
 profilers (ncu). Nothing is timed here; the benchmark is bench.py.
 
     python -m paper_1410_7170_gb300.profile_run --what solve_mixed|solve_fp64|sign64|dslash64|dslash32
-        [--lattice 16x16x16x16] [--stout 3]
+        [--lattice 16x16x16x16] [--stout 3] [--stencil-tps 1] [--sap-tps 1]
 
 The gauge field, right-hand side and solver settings are those of bench.py's 16^4
 workload (seeded links exp(i 0.5 H) smeared by 3 stout steps, rho = 1, mu = 0.01,
-one Gaussian right-hand side, tol 1e-8).
+one Gaussian right-hand side, tol 1e-8). Under a profiler the autotuner's timings are
+distorted, so --stencil-tps / --sap-tps fix the kernel variants (0 = autotune).
 """
 import argparse
 import os
@@ -29,17 +30,20 @@ def main():
                     choices=["solve_mixed", "solve_fp64", "sign64", "dslash64", "dslash32"])
     ap.add_argument("--lattice", default="16x16x16x16")
     ap.add_argument("--stout", type=int, default=3)
+    ap.add_argument("--stencil-tps", type=int, default=0)
+    ap.add_argument("--sap-tps", type=int, default=0)
     a = ap.parse_args()
     build.build()
     dims = tuple(int(v) for v in a.lattice.split("x"))
     U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1002, stout_steps=a.stout)).cuda()
     b = torch.from_numpy(synth.rhs_gaussian(dims, 2002)).cuda()
+    tune = dict(stencil_tps=a.stencil_tps, sap_tps=a.sap_tps)
     if a.what == "solve_mixed":
-        p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32)
+        p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, **tune)
     elif a.what == "solve_fp64":
-        p = ovl.params_default(precond=ovl.OVL_PREC_WILSON, precision=ovl.OVL_FP64, prec_max_iter=4)
+        p = ovl.params_default(precond=ovl.OVL_PREC_WILSON, precision=ovl.OVL_FP64, prec_max_iter=4, **tune)
     else:
-        p = ovl.params_default()
+        p = ovl.params_default(**tune)
     op = ovl.Overlap(U, dims, 1.0, 0.01, p)
     x = torch.zeros_like(b)
     if a.what.startswith("solve"):

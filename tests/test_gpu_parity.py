@@ -114,6 +114,26 @@ def test_sign_apply_matches_dense_sign(c1, tps):
     op.close()
 
 
+@pytest.mark.parametrize("tol", [1e-4, 1e-6, 1e-8, 1e-10])
+def test_adaptive_zolotarev_degree_keeps_accuracy(c1, tol):
+    """With adaptive_poles each sign application uses the smallest degree whose uniform
+    error is <= tol/10: the result still meets tol against the exact (dense) sign, and
+    agrees with the fixed 20-pole result to about tol."""
+    dims, U, rho, DN, S, aw = c1
+    b = synth.rhs_gaussian(dims, 2005)
+    ref = (S @ b.reshape(-1)).reshape(b.shape)
+    outs = {}
+    for adaptive in (0, 1):
+        p = params(lambda_min=0.98 * aw.min(), lambda_max=1.02 * aw.max(), n_poles=20, adaptive_poles=adaptive)
+        op = ovl.Overlap(U, dims, 1.0, 0.05, p)
+        out = torch.empty_like(dev(b))
+        op.sign_apply(out, dev(b), tol)
+        outs[adaptive] = host(out)
+        assert rel2(outs[adaptive], ref) < 3 * tol, (adaptive, rel2(outs[adaptive], ref))
+        op.close()
+    assert rel2(outs[1], outs[0]) < 4 * tol
+
+
 def test_lanczos_interval_encloses_spectrum(c1):
     dims, U, rho, DN, S, aw = c1
     op = ovl.Overlap(U, dims, 1.0, 0.05, ovl.params_default())
@@ -288,6 +308,31 @@ def test_sap_threads_per_site_variants_agree(dims):
         assert relmax(one[tps], one[1]) < 1e-5, (tps, relmax(one[tps], one[1]))
         assert abs(its[tps] - its[1]) <= 2, its
     assert max(res.values()) < 1.5e-4, res
+
+
+def test_profiling_counters_are_consistent():
+    """The instrumentation samples one multishift iteration per queued chunk: the timed
+    launches are a subset of all launches, with positive times and bytes."""
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_field(dims, 0.5, 1204, stout_steps=3)
+    b = torch.from_numpy(synth.rhs_gaussian(dims, 2204)).cuda()
+    op = ovl.Overlap(torch.from_numpy(U).cuda(), dims, 1.0, 0.01,
+                     ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32))
+    op.prof_enable(True)
+    op.prof_get(reset=True)
+    x = torch.zeros_like(b)
+    st, stats = op.ovl_solve(x, b, 1, 1e-8)
+    pr = op.prof_get(reset=True)
+    assert pr["valid"] == 1 and pr["launches"] > 0
+    for name in ("ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_f32"):
+        k = pr[name]
+        assert 0 < k["timed"] <= k["launches"], (name, k)
+        assert k["ms"] > 0 and 0 < k["timed_bytes"] <= k["bytes"], (name, k)
+    assert pr["ms_stencil_f64"]["launches"] == 2 * stats["ms_iters_fp64"]
+    assert pr["ms_shifts_f32"]["launches"] == stats["ms_iters_low"]
+    assert stats["t_sign_fp64"] > 0 and stats["t_sign_low"] > 0 and stats["t_prec"] > 0
+    assert stats["t_sign_fp64"] + stats["t_sign_low"] + stats["t_prec"] <= stats["seconds"]
+    op.close()
 
 
 def test_autotuner_reports_a_choice():
