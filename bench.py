@@ -63,6 +63,14 @@ def traffic_from_profiles(kernel):
     return None if k is None else k.get("dram_bytes_per_launch")
 
 
+def traffic_note(kernel):
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return json.load(f).get("kernels", {}).get(kernel, {}).get("note")
+    except OSError:
+        return None
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -273,7 +281,8 @@ def run_ours(args, rank, world, dist):
                    "sap_cycle_ms_tps1_2_4": [round(v, 4) for v in tuning_sap["ms"]]},
         "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": (achieved / peak) if achieved else None, "peak_kind": pkind,
-                     "traffic": traffic_from_profiles(dom), "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "traffic": traffic_from_profiles(dom), "traffic_note": traffic_note(dom),
+                     "algorithmic_bytes_per_launch": per_launch_bytes,
                      "launches": n_l, "timed_launches": kd["timed"], "avg_launch_us": kd["avg_ms"] * 1e3,
                      "kernels": {k: {"total_ms": v["total_ms"], "launches": v["launches"], "timed": v["timed"],
                                      "avg_us": v["avg_ms"] * 1e3,
