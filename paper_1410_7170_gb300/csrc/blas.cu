@@ -59,11 +59,12 @@ __global__ void k_caxpy(double ar, double ai, const double *__restrict__ x, doub
     }
 }
 
-// Multi-dot: blockIdx.y = vector index; partials[k][blockIdx.x] (complex)
+// Multi-dot: blockIdx.y = vector index; partials[k][blockIdx.x] (complex). Rows y >= m use
+// w itself, so an extra row gives (||w||^2, 0) in the same pass.
 template <typename T>
-__global__ void k_multidot_part(const T *__restrict__ base, long stride, const T *__restrict__ w, long nc,
+__global__ void k_multidot_part(const T *__restrict__ base, long stride, int m, const T *__restrict__ w, long nc,
                                 double *partials) {
-    const T *v = base + (long)blockIdx.y * stride;
+    const T *v = (int)blockIdx.y < m ? base + (long)blockIdx.y * stride : w;
     T a = 0, b = 0;
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += (long)gridDim.x * blockDim.x) {
         const T vr = v[2 * k], vi = v[2 * k + 1];
@@ -89,6 +90,28 @@ __global__ void k_multidot_sum(const double *partials, int nb, double *out) {
     if (threadIdx.x == 0) {
         out[2 * blockIdx.x] = s[0];
         out[2 * blockIdx.x + 1] = s[1];
+    }
+}
+
+// out = scale (w - sum_j h_j v_j) with h the complex dot products of a multi-dot (device
+// memory, FP64): the Gram-Schmidt update and normalisation of an Arnoldi step in one pass.
+template <typename T>
+__global__ void k_orth_scale(const T *__restrict__ base, long stride, int m, const double *__restrict__ h,
+                             double scale, const T *__restrict__ w, T *__restrict__ out, long nc) {
+    __shared__ T cs[2 * 128];
+    for (int k = threadIdx.x; k < 2 * m; k += blockDim.x) cs[k] = (T)(-h[k]);
+    __syncthreads();
+    const T sc = (T)scale;
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += (long)gridDim.x * blockDim.x) {
+        T ar = w[2 * k], ai = w[2 * k + 1];
+        for (int j = 0; j < m; j++) {
+            const T *v = base + (long)j * stride;
+            const T vr = v[2 * k], vi = v[2 * k + 1];
+            ar += cs[2 * j] * vr - cs[2 * j + 1] * vi;
+            ai += cs[2 * j] * vi + cs[2 * j + 1] * vr;
+        }
+        out[2 * k] = sc * ar;
+        out[2 * k + 1] = sc * ai;
     }
 }
 
@@ -177,7 +200,7 @@ cudaError_t dev_multidot(const double *base, long stride, int m, const double *w
     int gx = (int)((n / 2 + kBlock - 1) / kBlock);
     if (gx > kMdBlocks) gx = kMdBlocks;
     if (gx < 1) gx = 1;
-    k_multidot_part<double><<<dim3(gx, m), kBlock, 0, st>>>(base, stride, w, n / 2, partials);
+    k_multidot_part<double><<<dim3(gx, m), kBlock, 0, st>>>(base, stride, m, w, n / 2, partials);
     k_multidot_sum<<<m, kBlock, 0, st>>>(partials, gx, out);
     count_launches(2);
     return cudaGetLastError();
@@ -188,9 +211,25 @@ cudaError_t dev_multidot_f(const float *base, long stride, int m, const float *w
     int gx = (int)((n / 2 + kBlock - 1) / kBlock);
     if (gx > kMdBlocks) gx = kMdBlocks;
     if (gx < 1) gx = 1;
-    k_multidot_part<float><<<dim3(gx, m), kBlock, 0, st>>>(base, stride, w, n / 2, partials);
+    k_multidot_part<float><<<dim3(gx, m), kBlock, 0, st>>>(base, stride, m, w, n / 2, partials);
     k_multidot_sum<<<m, kBlock, 0, st>>>(partials, gx, out);
     count_launches(2);
+    return cudaGetLastError();
+}
+cudaError_t dev_multidot_norm_f(const float *base, long stride, int m, const float *w, long n, double *out,
+                                double *partials, cudaStream_t st) {
+    int gx = (int)((n / 2 + kBlock - 1) / kBlock);
+    if (gx > kMdBlocks) gx = kMdBlocks;
+    if (gx < 1) gx = 1;
+    k_multidot_part<float><<<dim3(gx, m + 1), kBlock, 0, st>>>(base, stride, m, w, n / 2, partials);
+    k_multidot_sum<<<m + 1, kBlock, 0, st>>>(partials, gx, out);
+    count_launches(2);
+    return cudaGetLastError();
+}
+cudaError_t dev_orth_scale_f(const float *base, long stride, int m, const double *h, double scale, const float *w,
+                             float *out, long n, cudaStream_t st) {
+    k_orth_scale<float><<<stream_grid(n / 2), kBlock, 0, st>>>(base, stride, m, h, scale, w, out, n / 2);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t dev_multiaxpy(const double *base, long stride, int m, const double *c, double *w, long n,

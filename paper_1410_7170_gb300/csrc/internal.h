@@ -112,6 +112,12 @@ cudaError_t dev_cdot_f(const float *x, const float *y, long n, double *res, RedS
 // multi-dot / multi-axpy with float vectors (accumulation in double)
 cudaError_t dev_multidot_f(const float *base, long stride, int m, const float *w, long n, double *out,
                            double *partials, cudaStream_t st);
+// out[0 .. 2m-1] = <base_j, w> (complex), out[2m] = ||w||^2, out[2m+1] = 0, in one pass.
+cudaError_t dev_multidot_norm_f(const float *base, long stride, int m, const float *w, long n, double *out,
+                                double *partials, cudaStream_t st);
+// out = scale (w - sum_j h_j base_j), h = the complex dots of dev_multidot_norm_f (device).
+cudaError_t dev_orth_scale_f(const float *base, long stride, int m, const double *h, double scale, const float *w,
+                             float *out, long n, cudaStream_t st);
 cudaError_t dev_multiaxpy_f(const float *base, long stride, int m, const double *c, float *w, long n,
                             cudaStream_t st);
 // Finite check of a flat array: *flag = 1 if some entry is NaN/Inf.

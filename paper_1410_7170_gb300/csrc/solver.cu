@@ -83,6 +83,15 @@ template <> struct Ops<float> {
         return sap_f32(c->g, sg, c->U32, (const float4 *)v, (float4 *)x, (float4 *)r, (float)m0, c->p.sap_cycles,
                        c->p.sap_mr_iters, c->stream);
     }
+    // [0, 2m) = <base_j, w>, [2m] = ||w||^2 in one pass over the basis
+    static cudaError_t multidot_norm(Ctx *c, const float *base, int m, const float *w, double *out) {
+        return dev_multidot_norm_f(base, c->n64, m, w, c->n64, out, c->d_md_part, c->stream);
+    }
+    // out = scale (w - sum_j h_j base_j), h on the device
+    static cudaError_t orth_scale(Ctx *c, const float *base, int m, const double *h, double scale, const float *w,
+                                  float *out) {
+        return dev_orth_scale_f(base, c->n64, m, h, scale, w, out, c->n64, c->stream);
+    }
     static constexpr bool kCgs2 = false;   // low-accuracy solves: one Gram-Schmidt pass unless it cancels
 };
 
@@ -190,7 +199,33 @@ static ovl_status fgmres(Ctx *c, Krylov<T> &k, T *x, const T *b, double tol, int
             // Gram-Schmidt: h = V^H w and ||w||^2 in one round trip; a second pass (CGS2)
             // always in FP64, and in FP32 only when the first pass cancels most of w.
             double hn = 0.0;
-            for (int pass = 0; pass < 2; pass++) {
+            bool next_done = false;   // V_{j+1} already written
+            if constexpr (!O::kCgs2) {
+                // one pass: the dots and ||w||^2 in one kernel; unless the pass cancels most of w,
+                // V_{j+1} = (w - V h) / hn in one more, with h read from device memory
+                CK(O::multidot_norm(c, k.V, j + 1, k.w, c->d_scal));
+                double tmp[2 * 128 + 2];
+                ST(c->fetch(c->d_scal, 2 * (j + 1) + 1, tmp));
+                double hsq = 0.0;
+                for (int i = 0; i <= j; i++) {
+                    h1[i] = cd(tmp[2 * i], tmp[2 * i + 1]);
+                    hsq += std::norm(h1[i]);
+                }
+                const double ww = tmp[2 * (j + 1)];
+                const double left = ww - hsq;
+                if (left > 0.1 * ww) {
+                    std::fill(h2.begin(), h2.end(), cd(0));
+                    hn = sqrt(left);
+                    if (hn > 0) CK(O::orth_scale(c, k.V, j + 1, c->d_scal, 1.0 / hn, k.w, k.V + (long)(j + 1) * n));
+                    next_done = true;
+                } else {   // cancellation: subtract this pass, then a second full pass below
+                    std::vector<cd> neg(j + 1);
+                    for (int i = 0; i <= j; i++) neg[i] = -h1[i];
+                    ST(upload_coef(c, neg));
+                    CK(O::multiaxpy(c, k.V, j + 1, c->d_coef, k.w));
+                }
+            }
+            for (int pass = next_done ? 2 : (O::kCgs2 ? 0 : 1); pass < 2; pass++) {
                 std::vector<cd> &hh = pass == 0 ? h1 : h2;
                 CK(O::multidot(c, k.V, j + 1, k.w, c->d_scal));
                 CK(O::norm2(c, k.w, c->d_scal + 2 * (j + 1)));
@@ -225,7 +260,7 @@ static ovl_status fgmres(Ctx *c, Krylov<T> &k, T *x, const T *b, double tol, int
                 c->err = "Krylov solver: non-finite Arnoldi coefficient";
                 return OVL_EBREAKDOWN;
             }
-            if (hn > 0) CK(O::axpby(c, 1.0 / hn, k.w, 0.0, k.V + (long)(j + 1) * n));
+            if (hn > 0 && !next_done) CK(O::axpby(c, 1.0 / hn, k.w, 0.0, k.V + (long)(j + 1) * n));
             // rotations
             for (int i = 0; i < j; i++) {
                 const cd a = H[(size_t)i * m + j], bq = H[(size_t)(i + 1) * m + j];
