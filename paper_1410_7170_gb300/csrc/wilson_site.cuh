@@ -183,6 +183,62 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const LT *__restrict__ U,
     }
 }
 
+// The hops of direction MU for two input fields at once: each link is loaded (for FP32:
+// and its third row rebuilt) once and applied to both.
+template <int MU, bool First, typename R, typename LT, typename ST>
+__device__ __forceinline__ void hop_dir2(const Geom &g, const LT *__restrict__ U, ST in0, ST in1, int p, int i,
+                                         const int x[4], cpx<R> acc0[12], cpx<R> acc1[12]) {
+    const int q = 1 - p;
+    {   // forward neighbour x + mu, link U_mu(x) stored at (p, i)
+        int y[4] = {x[0], x[1], x[2], x[3]};
+        y[MU] = (x[MU] + 1 == g.L[MU]) ? 0 : x[MU] + 1;
+        const int j = eo_index(g, y);
+        const bool neg = MU == 0 && g.antiperiodic && x[0] == g.L[0] - 1;
+        cpx<R> u[3][3];
+        load_link<R>(U, g.Vh, p, MU, i, u);
+#pragma unroll
+        for (int f = 0; f < 2; f++) {
+            cpx<R> s[12], h0[3], h1[3], a0[3], a1[3];
+            load_spinor<R>(f ? in1 : in0, g.Vh, q, j, s);
+            proj_fwd(MU, s, h0, h1);
+            if (MU == 0) flip_half(h0, h1, neg);
+            su3_mul(u, h0, a0);
+            su3_mul(u, h1, a1);
+            acc_fwd<First>(MU, f ? acc1 : acc0, a0, a1);
+        }
+    }
+    {   // backward neighbour x - mu, link U_mu(x - mu)^H stored at (q, j)
+        int y[4] = {x[0], x[1], x[2], x[3]};
+        y[MU] = (x[MU] == 0) ? g.L[MU] - 1 : x[MU] - 1;
+        const int j = eo_index(g, y);
+        const bool neg = MU == 0 && g.antiperiodic && x[0] == 0;
+        cpx<R> u[3][3];
+        load_link<R>(U, g.Vh, q, MU, j, u);
+#pragma unroll
+        for (int f = 0; f < 2; f++) {
+            cpx<R> s[12], h0[3], h1[3], a0[3], a1[3];
+            load_spinor<R>(f ? in1 : in0, g.Vh, q, j, s);
+            proj_bwd(MU, s, h0, h1);
+            if (MU == 0) flip_half(h0, h1, neg);
+            su3_dag_mul(u, h0, a0);
+            su3_dag_mul(u, h1, a1);
+            acc_bwd(MU, f ? acc1 : acc0, a0, a1);
+        }
+    }
+}
+
+// Hopping sums of two fields at one site (links loaded once for both).
+template <typename R, typename LT, typename ST>
+__device__ __forceinline__ void wilson_hop2(const Geom &g, const LT *__restrict__ U, ST in0, ST in1, int p, int i,
+                                            cpx<R> acc0[12], cpx<R> acc1[12]) {
+    int x[4];
+    eo_coords(g, p, i, x);
+    hop_dir2<0, true, R>(g, U, in0, in1, p, i, x, acc0, acc1);
+    hop_dir2<1, false, R>(g, U, in0, in1, p, i, x, acc0, acc1);
+    hop_dir2<2, false, R>(g, U, in0, in1, p, i, x, acc0, acc1);
+    hop_dir2<3, false, R>(g, U, in0, in1, p, i, x, acc0, acc1);
+}
+
 // Hopping sum H(x) = sum_mu [(1-g_mu) U_mu(x) in(x+mu) + (1+g_mu) U_mu(x-mu)^H in(x-mu)]
 // for the site (p, i); `in` is any spinor storage accepted by load_spinor.
 template <typename R, typename LT, typename ST>
