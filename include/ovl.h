@@ -133,8 +133,9 @@ ovl_status ovl_params_default(ovl_params *p);
  * p: NULL = defaults. cuda_stream: a cudaStream_t the context issues all work on
  * (NULL = the context creates its own non-blocking stream).
  * If lambda_min/lambda_max are 0 they are estimated here by Lanczos on Q^2.
- * The Wilson preconditioner mass defaults to m0^def (Eq. default_m) with sigma_min
- * from a fixed number of power iterations on D_W(0) (Sec. 5.1).
+ * The Wilson preconditioner mass defaults to m0^def (Eq. default_m). sigma_min, the
+ * smallest real part of the eigenvalues of D_W(0), is estimated by the smallest singular
+ * value of D_W(0) (Lanczos on (Gamma5 D_W(0))^2).
  * On success *ctx is a new context; on error *ctx is NULL. */
 ovl_status ovl_create(ovl_ctx **ctx, const double *gauge, const int dims[4],
                       double rho_in, double mu, const ovl_params *p, void *cuda_stream);

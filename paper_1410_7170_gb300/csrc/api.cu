@@ -651,8 +651,9 @@ static double tridiag_eig(const std::vector<double> &a, const std::vector<double
 
 // Lanczos on Q^2 in FP32 (no re-orthogonalisation: extremal Ritz values converge
 // first and spurious copies do not move them).
-ovl_status Ctx::lanczos_bounds(double *lmin, double *lmax) {
+ovl_status Ctx::lanczos_bounds(double *lmin, double *lmax, double m0) {
     Ctx *c = this;
+    const float mq = (float)(isnan(m0) ? m0_ker : m0);   // Q = Gamma5 D_W(mq)
     const long nf = n64;   // floats per FP32 vector
     float *v0, *v1, *w, *tt;
     void *buf;
@@ -678,8 +679,8 @@ ovl_status Ctx::lanczos_bounds(double *lmin, double *lmax) {
     const int maxit = 600;
     double beta_prev = 0.0;
     for (int j = 0; j < maxit; j++) {
-        CK(wilson_f32(g, U32, (const float4 *)v1, (float4 *)tt, (float)m0_ker, 1, 1.f, nullptr, 0.f, stream));
-        CK(wilson_f32(g, U32, (const float4 *)tt, (float4 *)w, (float)m0_ker, 1, 1.f, nullptr, 0.f, stream));
+        CK(wilson_f32(g, U32, (const float4 *)v1, (float4 *)tt, mq, 1, 1.f, nullptr, 0.f, stream));
+        CK(wilson_f32(g, U32, (const float4 *)tt, (float4 *)w, mq, 1, 1.f, nullptr, 0.f, stream));
         if (j > 0) CK(dev_axpby_f((float)(-beta_prev), v0, 1.f, w, nf, stream));
         double d2[2];
         CK(dev_cdot_f(v1, w, nf, d_scal, rs, stream));
@@ -716,33 +717,17 @@ ovl_status Ctx::lanczos_bounds(double *lmin, double *lmax) {
 
 // sigma~_max of D_W(0) by power iteration; sigma~_min = 8 - sigma~_max rounded up to
 // one decimal (Sec. 5.1).
+// sigma_min of Eq. (default_m): the smallest real part of the eigenvalues of D_W(0). It is
+// estimated by the smallest singular value of D_W(0), i.e. the smallest |eigenvalue| of the
+// Hermitian Q(0) = Gamma5 D_W(0), from the Lanczos run on Q(0)^2 (its extreme eigenvalues
+// converge fast and no basis is stored). For the near-real low modes of smeared fields the two
+// quantities are close. (Sec. 5.1's power-iteration guess 8 - sigma_max, rounded up, only
+// bounds the range of the paper's m0_prec scan; taken as sigma_min it put m0_prec near the
+// critical mass and made the Wilson solves much slower.)
 ovl_status Ctx::sigma_min_estimate(double *smin) {
-    Ctx *c = this;
-    const long nf = n64;
-    void *buf;
-    ST(alloc(&buf, (size_t)nf * sizeof(float) * 2));
-    float *v = (float *)buf, *w = v + nf;
-    std::vector<float> h(nf);
-    uint64_t st = 0xD1B54A32D192ED03ull;
-    for (long i = 0; i < nf; i++) {
-        st ^= st << 13; st ^= st >> 7; st ^= st << 17;
-        h[i] = (float)((double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5);
-    }
-    CK(cudaMemcpyAsync(v, h.data(), nf * sizeof(float), cudaMemcpyHostToDevice, stream));
-    double nn;
-    ST(norm2_f(v, &nn));
-    CK(dev_axpby_f((float)(1.0 / sqrt(nn)), v, 0.f, v, nf, stream));
-    double ray = 0.0;
-    for (int it = 0; it < 50; it++) {
-        CK(wilson_f32(g, U32, (const float4 *)v, (float4 *)w, 0.f, 0, 1.f, nullptr, 0.f, stream));
-        double d2[2];
-        CK(dev_cdot_f(v, w, nf, d_scal, rs, stream));
-        ST(fetch(d_scal, 2, d2));
-        ray = d2[0];
-        ST(norm2_f(w, &nn));
-        CK(dev_axpby_f((float)(1.0 / sqrt(nn)), w, 0.f, v, nf, stream));
-    }
-    *smin = ceil(10.0 * (8.0 - ray)) / 10.0;
+    double lo, hi;
+    ST(lanczos_bounds(&lo, &hi, 0.0));
+    *smin = lo;
     return OVL_OK;
 }
 
@@ -1030,9 +1015,13 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
     }
     ST(c->set_zolotarev());
     // preconditioner mass m0^def (Eq. default_m) unless given
-    ST(c->sigma_min_estimate(&c->sigma_min));
-    if (isnan(c->p.m0_prec)) c->m0_prec = (-c->m0_ker - c->sigma_min) * c->rho + c->m0_ker;
-    else c->m0_prec = c->p.m0_prec;
+    c->sigma_min = NAN;
+    if (isnan(c->p.m0_prec) && c->p.precond != OVL_PREC_NONE) {
+        ST(c->sigma_min_estimate(&c->sigma_min));
+        c->m0_prec = (-c->m0_ker - c->sigma_min) * c->rho + c->m0_ker;
+    } else {
+        c->m0_prec = c->p.m0_prec;
+    }
     return OVL_OK;
 }
 

@@ -383,10 +383,10 @@ ovl_status wilson_solve_eo(Ctx *c, const double2 *b, double2 *x, double m0, doub
 
 int batch_size_for(Ctx *c, int want);
 // Most accurate sign request the lower-precision multishift serves in the mixed modes:
-// FP32 vectors, FP16-stored directions (11 significant bits, per-site scale), BF16-stored
-// directions (8 significant bits).
+// FP32 vectors (the accuracy floor of the inner requests too), FP16-stored directions (11
+// significant bits, per-site scale), BF16-stored directions (8 significant bits).
 static double low_sign_floor(int precision) {
-    return precision == OVL_MIXED_BF16 ? 1e-2 : precision == OVL_MIXED_HALF ? 1e-3 : 1e-5;
+    return precision == OVL_MIXED_BF16 ? 1e-2 : precision == OVL_MIXED_HALF ? 1e-3 : 1e-6;
 }
 
 

@@ -147,7 +147,7 @@ struct Ctx {
     ovl_status sign32_batch(const float4 *b, float4 *out, int nrhs, const double *tol, int mode);
     template <typename ST, typename Init, typename Iter>
     ovl_status msb_run(int nrhs, const double *tol, int n, int slot, Init init_fn, Iter iter_fn, long *iters_out);
-    ovl_status lanczos_bounds(double *lmin, double *lmax);
+    ovl_status lanczos_bounds(double *lmin, double *lmax, double m0 = NAN);   // |eigenvalues| of Q(m0), default m0_ker
     ovl_status sigma_min_estimate(double *smin);
     ovl_status set_zolotarev();
     ovl_status autotune();

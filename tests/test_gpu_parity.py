@@ -150,6 +150,28 @@ def test_lanczos_interval_encloses_spectrum(c1):
     op.close()
 
 
+def test_sigma_min_and_default_preconditioner_mass(c1):
+    """m0_prec defaults to m0^def of Eq. (default_m) with sigma_min, the smallest real part of
+    the eigenvalues of D_W(0), estimated by the smallest singular value of D_W(0). Both are
+    checked against the dense oracle: the estimate matches the singular value (0.820 here), and
+    lies within 0.2 of the exact smallest real part (0.692: the leftmost eigenvalues of this
+    rough 4^4 field are a complex pair)."""
+    dims, U, rho, DN, S, aw = c1
+    DW0 = dense.wilson_matrix(U, dims, 0.0).toarray()
+    smin_exact = np.linalg.svd(DW0, compute_uv=False).min()
+    re_min = np.linalg.eigvals(DW0).real.min()
+    op = ovl.Overlap(U, dims, 1.0, 0.05, ovl.params_default(precond=ovl.OVL_PREC_WILSON))
+    info = op.info()
+    assert abs(info["sigma_min"] - smin_exact) < 1e-3 * smin_exact + 1e-4, (info["sigma_min"], smin_exact)
+    assert abs(info["sigma_min"] - re_min) < 0.2, (info["sigma_min"], re_min)
+    assert abs(info["m0_prec"] - dense.default_prec_mass(info["rho"], -1.0, info["sigma_min"])) < 1e-12
+    op.close()
+    # an explicit m0_prec wins; without a preconditioner no estimate is made
+    op = ovl.Overlap(U, dims, 1.0, 0.05, ovl.params_default(precond=ovl.OVL_PREC_WILSON, m0_prec=-0.3))
+    assert op.info()["m0_prec"] == -0.3 and np.isnan(op.info()["sigma_min"])
+    op.close()
+
+
 def test_sign_apply_matches_sparse_oracle_8x8x8x8():
     dims = (8, 8, 8, 8)
     U = synth.gauge_field(dims, 0.5, 1102, stout_steps=3)
