@@ -9,8 +9,8 @@
 //   FP32 spinor: float4  [p][6 pairs of spin-colour][Vh] ( 96 B per site)
 //   FP16 spinor: uint4 (8 halves) [p][3][Vh] + float norm [p][Vh] (48+4 B per site)
 //   BF16 spinor: uint4 (8 bfloat16) [p][3][Vh], no norm              (48 B per site)
-//   FP64 link:   double2 [p][mu][9][Vh]   all 18 reals of U_mu(x)
-//   FP32 link:   float4  [p][mu][3][Vh]   rows 0 and 1 (12 reals)
+//   FP64 link:   double2 [p][mu][9][Vh]   all 18 reals of -1/2 U_mu(x)
+//   FP32 link:   float4  [p][mu][3][Vh]   rows 0 and 1 (12 reals) of -1/2 U_mu(x)
 // The FP32 stencils rebuild row 2 of an SU(3) link in registers as conj(row0 x row1);
 // the FP64 stencils, bound by the FP64 pipes rather than by memory, load all 18 reals
 // instead (the rebuild would cost about a fifth of their FP64 instructions).
@@ -225,12 +225,17 @@ __device__ __forceinline__ void store_spinor(Bf16Spinor f, int Vh, int p, int i,
     }
 }
 
-// Links: rows 0 and 1 stored, row 2 = conj(row0 x row1).
+// Links are stored as V = kLinkScale U: the factor -1/2 of the hopping term of Eq.
+// (Wilson-Dirac) is folded into them, so that a site's result (m0+4) psi + hop is one FMA
+// per real. For U in SU(3), row 2 = conj(row0 x row1); for V = s U that becomes
+// row2(V) = conj(row0(V) x row1(V)) / s.
+constexpr double kLinkScale = -0.5;
 template <typename R>
 __device__ __forceinline__ void reconstruct_row2(cpx<R> u[3][3]) {
-    u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-    u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-    u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    constexpr R inv = (R)(1.0 / kLinkScale);
+    u[2][0] = inv * conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+    u[2][1] = inv * conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+    u[2][2] = inv * conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
 }
 constexpr int kLink64Words = 9;   // double2 words per FP64 link
 template <typename R>

@@ -35,7 +35,7 @@ int device_sm_count() {
 }
 
 // ------------------------------------------------------------------ gauge upload
-// One thread per (site, mu): SU(3) check, then rows 0 and 1 into both precisions.
+// One thread per (site, mu): SU(3) check, then -1/2 U in both precisions (FP32: rows 0 and 1).
 __global__ void k_pack_gauge(Geom g, const double2 *__restrict__ lex, double2 *u64, float4 *u32, int *bad,
                              double tol) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,6 +71,11 @@ __global__ void k_pack_gauge(Geom g, const double2 *__restrict__ lex, double2 *u
     x[2] = r % g.L[2]; r /= g.L[2];
     x[1] = r % g.L[1]; x[0] = r / g.L[1];
     const int p = (x[0] + x[1] + x[2] + x[3]) & 1, i = s >> 1;
+    // stored as kLinkScale U (the hopping term's -1/2 folded in)
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) u[a][b] = kLinkScale * u[a][b];
     double2 *d64 = u64 + ((size_t)(p * 4 + mu) * kLink64Words) * g.Vh + i;
 #pragma unroll
     for (int c = 0; c < 9; c++) d64[(size_t)c * g.Vh] = make_double2(u[c / 3][c % 3].re, u[c / 3][c % 3].im);
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_wilson4(Geom g,
 #pragma unroll
         for (int e = 0; e < C::CPC; e++) {
             const int cix = j * C::CPC + e;
-            res[e] = m4 * own[e] - (R)0.5 * acc[cix];
+            res[e] = m4 * own[e] + acc[cix];
             if (g5 && cix < 6) res[e] = -res[e];
             res[e] = a * res[e];
         }

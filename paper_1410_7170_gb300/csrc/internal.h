@@ -133,6 +133,7 @@ struct MsState {
     int status;                // 0 ok, 1 breakdown / non-finite scalar
     double bb;                 // ||b||^2
     double rr;                 // ||r_k||^2 (base residual)
+    double pp;                 // ||p_0||^2 by the recurrence ||p_k||^2 = ||r_k||^2 + b_{k-1}^2 ||p_{k-1}||^2
     double alpha, alpha_prev, beta_prev;
     double tol;                // target relative accuracy of the rational function
     double sigma[kMaxPoles];   // shifts

@@ -21,7 +21,7 @@
 //   y += (w_l a_k zeta_{k+1}) p~_l,   p~_l = r_{k+1} + (b_k zeta_{k+1}/zeta_k) p~_l.
 //
 // One iteration = three kernels, all scalars stay on the device:
-//   ms_q:      t = Q p_0 (stencil with gamma5),       reduce ||t||^2, ||p_0||^2 -> alpha
+//   ms_q:      t = Q p_0 (stencil with gamma5),       reduce ||t||^2 -> alpha
 //   ms_r:      r -= alpha (gamma5 D_W t + sigma_0 p_0), reduce ||r||^2 -> beta, shift scalars
 //   ms_shifts: y += sum_l w~_l p~_l ; p~_l = r + b~_l p~_l   (pure streaming)
 // (p_0, Q^2 p_0) = ||Q p_0||^2 because Q is Hermitian (Eq. gamma_5_symmetry).
@@ -38,10 +38,13 @@ namespace ovl {
 
 namespace {
 
+// alpha = (r, r) / (p, (Q^2 + sigma_0) p) with (p, Q^2 p) = ||Q p||^2 (v[0], reduced by ms_q)
+// and ||p||^2 from the scalar recurrence ||p_k||^2 = ||r_k||^2 + beta^2 ||p_{k-1}||^2, which
+// holds because r_k is orthogonal to p_{k-1} in CG; this spares ms_q a second reduction.
 struct AlphaFin {
     MsState *s;
     __device__ void operator()(const double *v) const {
-        const double pAp = v[0] + s->sigma[0] * v[1];
+        const double pAp = v[0] + s->sigma[0] * s->pp;
         const double a = s->rr / pAp;
         if (!(pAp > 0.0) || !isfinite(a)) {
             s->status = 1;
@@ -104,6 +107,7 @@ struct ShiftFin {
             if (s->hist && s->iter < s->hist_cap) s->hist[s->iter] = nupd;
             s->alpha_prev = a;
             s->beta_prev = beta;
+            s->pp = rr_new + beta * beta * s->pp;
             s->rr = rr_new;
             s->iter += 1;
             if (!any) s->done = 2;   // finish this iteration's shift updates, then stop
@@ -111,13 +115,13 @@ struct ShiftFin {
     }
 };
 
-// t = gamma5 D_W(m) p0 ; reduce ||t||^2, ||p0||^2
+// t = gamma5 D_W(m) p0 ; reduce ||t||^2
 template <typename R, typename LT, typename ST>
 __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, const LT *__restrict__ U, R m4, MsState *s,
                                                  const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs,
                                                  int spb) {
     if (s->done) return;
-    R v[2] = {0, 0};   // per-thread sums in R; FP64 from the warp sums on (grid_reduce)
+    R v[1] = {0};   // per-thread sums in R; FP64 from the warp sums on (grid_reduce)
     const bool lane_has_sites = threadIdx.x < spb;
     for (int k = blockIdx.x * spb + threadIdx.x; lane_has_sites && k < g.V; k += gridDim.x * spb) {
         int p, i;
@@ -128,16 +132,12 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, co
         wilson_combine<R>(m4, own, hop, res);
         apply_g5(res);
         store_spinor<R>(t, g.Vh, p, i, res);
-        R a0 = 0, a1 = 0;   // per-site sums in the arithmetic type, across sites in FP64
+        R a0 = 0;   // per-site sums in the arithmetic type, across sites in FP64
 #pragma unroll
-        for (int c = 0; c < 12; c++) {
-            a0 += norm2(res[c]);
-            a1 += norm2(own[c]);
-        }
+        for (int c = 0; c < 12; c++) a0 += norm2(res[c]);
         v[0] += a0;
-        v[1] += a1;
     }
-    grid_reduce<2>(v, rs, AlphaFin{s});
+    grid_reduce<1>(v, rs, AlphaFin{s});
 }
 
 // r -= alpha (gamma5 D_W(m) t + sigma0 p0) ; reduce ||r||^2 ; shift scalars
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q4(Geom g, c
                                                   const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs) {
     if (s->done) return;
     using C = Chunk<ST>;
-    R v[2] = {0, 0};
+    R v[1] = {0};
     const long nthr = 4L * g.V;
     for (long base = (long)blockIdx.x * blockDim.x; base < nthr; base += (long)gridDim.x * blockDim.x) {
         const long tt = base + threadIdx.x;
@@ -195,21 +195,19 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q4(Geom g, c
             if ((j & 3) != q) continue;
             cpx<R> own[C::CPC], res[C::CPC];
             C::template load<R>(p0, g.Vh, p, i, j, own);
-            R a0 = 0, a1 = 0;
+            R a0 = 0;
 #pragma unroll
             for (int e = 0; e < C::CPC; e++) {
                 const int cix = j * C::CPC + e;
-                res[e] = m4 * own[e] - (R)0.5 * acc[cix];
+                res[e] = m4 * own[e] + acc[cix];
                 if (cix < 6) res[e] = -res[e];
                 a0 += norm2(res[e]);
-                a1 += norm2(own[e]);
             }
             v[0] += a0;
-            v[1] += a1;
             C::template store<R>(t, g.Vh, p, i, j, res);
         }
     }
-    grid_reduce<2>(v, rs, AlphaFin{s});
+    grid_reduce<1>(v, rs, AlphaFin{s});
 }
 
 template <typename R, typename LT, typename ST>
@@ -242,7 +240,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r4(Geom g, c
             R a0 = 0;
             for (int e = 0; e < C::CPC; e++) {
                 const int cix = j * C::CPC + e;
-                cpx<R> res = m4 * own[e] - (R)0.5 * acc[cix];
+                cpx<R> res = m4 * own[e] + acc[cix];
                 if (cix < 6) res = -res;
                 rv[e] = rv[e] - alpha * (res + sig0 * pp[e]);
                 a0 += norm2(rv[e]);
@@ -337,6 +335,7 @@ struct InitFin {
     __device__ void operator()(const double *v) const {
         s->bb = v[0];
         s->rr = v[0];
+        s->pp = v[0];   // p_0 = b
         if (v[0] == 0.0) s->done = 1;
         if (!isfinite(v[0])) {
             s->status = 1;

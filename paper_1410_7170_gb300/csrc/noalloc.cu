@@ -31,7 +31,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 
-// Every link into the FP64 even-odd link layout of the library (all 18 reals).
+// Every link into the FP64 even-odd link layout of the library (all 18 reals of
+// kLinkScale U, the form the stencil expects).
 __global__ void k_noalloc_pack_links(Geom g, const double2 *__restrict__ lex) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)g.V * 4) return;
@@ -45,7 +46,10 @@ __global__ void k_noalloc_pack_links(Geom g, const double2 *__restrict__ lex) {
     double2 *links = reinterpret_cast<double2 *>(g_noalloc_scratch);
     double2 *d = links + ((size_t)(p * 4 + mu) * kLink64Words) * g.Vh + i;
 #pragma unroll
-    for (int c = 0; c < 9; c++) d[(size_t)c * g.Vh] = lex[(size_t)t * 9 + c];
+    for (int c = 0; c < 9; c++) {
+        const double2 w = lex[(size_t)t * 9 + c];
+        d[(size_t)c * g.Vh] = make_double2(kLinkScale * w.x, kLinkScale * w.y);
+    }
 }
 
 std::mutex g_noalloc_mu;

@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(256 * TPS, 1)
             gather_part<TPS, C>(X, nb, t, c0, hop);
             load_comps<C>(x, g.Vh, p, i, c0, own);
 #pragma unroll
-            for (int c = 0; c < C; c++) res[c] = res[c] - (m4 * own[c] - (R)0.5 * hop[c]);
+            for (int c = 0; c < C; c++) res[c] = res[c] - (m4 * own[c] + hop[c]);
         }
     }
     for (int it = 0; it < mr_iters; it++) {
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(256 * TPS, 1)
             gather_part<TPS, C>(X, nb, t, c0, hop);
 #pragma unroll
             for (int c = 0; c < C; c++) {
-                q[c] = m4 * res[c] - (R)0.5 * hop[c];
+                q[c] = m4 * res[c] + hop[c];
                 a0 += q[c].re * res[c].re + q[c].im * res[c].im;   // Re <q, s>
                 a1 += q[c].re * res[c].im - q[c].im * res[c].re;   // Im <q, s>
                 a2 += norm2(q[c]);

@@ -240,7 +240,8 @@ __device__ __forceinline__ void wilson_hop2(const Geom &g, const LT *__restrict_
 }
 
 // Hopping sum H(x) = sum_mu [(1-g_mu) U_mu(x) in(x+mu) + (1+g_mu) U_mu(x-mu)^H in(x-mu)]
-// for the site (p, i); `in` is any spinor storage accepted by load_spinor.
+// for the site (p, i), times -1/2 (the stored links are -1/2 U); `in` is any spinor storage
+// accepted by load_spinor.
 template <typename R, typename LT, typename ST>
 __device__ __forceinline__ void wilson_hop(const Geom &g, const LT *__restrict__ U, ST in, int p, int i,
                                            cpx<R> acc[12]) {
@@ -252,11 +253,12 @@ __device__ __forceinline__ void wilson_hop(const Geom &g, const LT *__restrict__
     hop_dir<3, false, R>(g, U, in, p, i, x, acc);
 }
 
-// res = (m0+4) own - 1/2 hop
+// res = (m0+4) own + hop, where hop (formed with the stored links -1/2 U) is -1/2 times the
+// hopping sum H(x): one FMA per real
 template <typename R>
 __device__ __forceinline__ void wilson_combine(R m4, const cpx<R> own[12], const cpx<R> hop[12], cpx<R> res[12]) {
 #pragma unroll
-    for (int c = 0; c < 12; c++) res[c] = m4 * own[c] - (R)0.5 * hop[c];
+    for (int c = 0; c < 12; c++) res[c] = cpx<R>{fma_r(m4, own[c].re, hop[c].re), fma_r(m4, own[c].im, hop[c].im)};
 }
 
 }  // namespace ovl
