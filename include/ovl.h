@@ -104,6 +104,12 @@ typedef struct {
     int adaptive_poles;     /* 1 (default): each sign application uses the smallest Zolotarev degree
                                n <= n_poles whose uniform error delta(k, n) is <= 1/10 of its requested
                                accuracy; 0: always n_poles */
+    int n_deflate;          /* k > 0: deflate the k eigenpairs of Q of smallest |lambda| (Sec. 5.2):
+                               computed once at ovl_create (FP64 thick-restart Krylov-Schur on Q^2),
+                               applied exactly, the sign iteration runs on the projected vector and its
+                               interval starts at 0.9 |lambda_{k+1}|. 0 (default): no deflation; <= 48 */
+    double deflate_tol;     /* eigenpair accuracy: Ritz residual of Q^2 <= deflate_tol * lambda_max^2
+                               (default 1e-13) */
 } ovl_params;
 
 /* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
@@ -155,6 +161,21 @@ ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, double m0, dou
  * and the measured ms per full-lattice stencil application of each variant
  * (ms[0..3] = FP64 x1, FP64 x4, FP32 x1, FP32 x4; zeros when forced). Nullable outputs. */
 ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, float *ms);
+
+/* Deflation state (Sec. 5.2): k deflated pairs, their eigenvalues lambda[k] (signed, by
+ * increasing modulus; nullable), |lambda_{k+1}| (the new lower end of the sign interval),
+ * the setup time in seconds, max_i ||Q xi_i - lambda_i xi_i|| and the Q^2 applications the
+ * eigensolver needed. k = 0 without deflation. */
+ovl_status ovl_deflation_info(const ovl_ctx *ctx, int *k, double *lambda, double *lambda_next, double *setup_s,
+                              double *resid_max, long *matvecs);
+
+/* Host utility: eigenvalues w[n] (ascending) and eigenvectors Z (n x n complex, row-major,
+ * column j for w[j]) of the n x n complex Hermitian matrix A (row-major, interleaved re/im,
+ * 2 n^2 doubles; not modified), by cyclic Jacobi rotations. The library uses it for the
+ * Rayleigh-Ritz steps of the low-mode eigensolver (an implementation choice; the paper
+ * computes its eigenpairs with PARPACK). OVL_EINVAL for n < 1 or NULL pointers, OVL_ENOCONV
+ * if 100 sweeps do not converge. */
+ovl_status ovl_hermitian_eig(int n, const double *A, double *w, double *Z);
 
 /* Threads per block site chosen for the FP32 Schwarz block solves of the Wilson
  * preconditioner (Sec. 5.1 smoother; an implementation choice, the paper has no

@@ -40,7 +40,8 @@ class ovl_params(ctypes.Structure):
         ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_iters", ctypes.c_int),
         ("prec_restart", ctypes.c_int), ("prec_max_iter", ctypes.c_int), ("rhs_block", ctypes.c_int),
         ("use_graphs", ctypes.c_int), ("check_every", ctypes.c_int), ("stencil_tps", ctypes.c_int),
-        ("sap_tps", ctypes.c_int), ("adaptive_poles", ctypes.c_int),
+        ("sap_tps", ctypes.c_int), ("adaptive_poles", ctypes.c_int), ("n_deflate", ctypes.c_int),
+        ("deflate_tol", ctypes.c_double),
     ]
 
 
@@ -95,7 +96,7 @@ class ovl_prof(ctypes.Structure):
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
-           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
+           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
            "ovl_apply_n", "ovl_dslash_time_n", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
@@ -126,6 +127,9 @@ def lib():
         L.wilson_solve.argtypes = [P, P, P, D, D, ctypes.POINTER(I_)]
         L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
         L.ovl_tuning_sap.argtypes = [P, ctypes.POINTER(I_), P]
+        L.ovl_hermitian_eig.argtypes = [I_, P, P, P]
+        L.ovl_deflation_info.argtypes = [P, ctypes.POINTER(I_), P, ctypes.POINTER(D), ctypes.POINTER(D),
+                                         ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
         L.wilson_apply_noalloc.argtypes = [P, P, P, P, D, I_, P]
         L.ovl_dslash_time.argtypes = [P, I_, I_, ctypes.POINTER(D)]
         L.wilson_apply_n.argtypes = [P, P, P, I_, D]
@@ -255,6 +259,29 @@ def ovl_tuning(ctx):
     return {"tps64": a.value, "tps32": b.value, "ms": ms.tolist()}
 
 
+def hermitian_eig(A):
+    """Eigenvalues (ascending) and eigenvectors (columns) of a complex Hermitian matrix (host)."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    w = np.empty(n)
+    Z = np.empty((n, n), dtype=np.complex128)
+    _check(lib().ovl_hermitian_eig(int(n), _ptr(A), _ptr(w, True), _ptr(Z, True)))
+    return w, Z
+
+
+def ovl_deflation_info(ctx):
+    import numpy as np
+    k = ctypes.c_int()
+    _check(lib().ovl_deflation_info(ctx, ctypes.byref(k), None, None, None, None, None), ctx)
+    lam = np.zeros(max(k.value, 1))
+    nxt, t, res, mv = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_long()
+    _check(lib().ovl_deflation_info(ctx, None, _ptr(lam, True), ctypes.byref(nxt), ctypes.byref(t),
+                                    ctypes.byref(res), ctypes.byref(mv)), ctx)
+    return {"k": k.value, "lambda": lam[:k.value].tolist(), "lambda_next": nxt.value, "setup_s": t.value,
+            "resid_max": res.value, "matvecs": mv.value}
+
+
 def ovl_tuning_sap(ctx):
     import numpy as np
     a = ctypes.c_int()
@@ -345,6 +372,9 @@ class Overlap:
 
     def tuning_sap(self):
         return ovl_tuning_sap(self.ctx)
+
+    def deflation_info(self):
+        return ovl_deflation_info(self.ctx)
 
     def dslash_time(self, precision, reps=20):
         return ovl_dslash_time(self.ctx, precision, reps)

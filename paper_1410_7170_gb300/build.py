@@ -14,9 +14,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libovl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["dslash.cu", "blas.cu", "multishift.cu", "solver.cu", "api.cu", "sap.cu", "multirhs.cu",
+CU_SOURCES = ["dslash.cu", "blas.cu", "multishift.cu", "solver.cu", "api.cu", "sap.cu", "multirhs.cu", "deflate.cu",
               "noalloc.cu", "server.cu"]
-CXX_SOURCES = ["zolotarev.cpp"]
+CXX_SOURCES = ["zolotarev.cpp", "eig_host.cpp"]
 
 
 def _nvcc():

@@ -61,6 +61,8 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->stencil_tps = 0;
     p->sap_tps = 0;
     p->adaptive_poles = 1;
+    p->n_deflate = 0;
+    p->deflate_tol = 1e-13;
     return OVL_OK;
 }
 
@@ -86,6 +88,8 @@ static ovl_status validate_params(const ovl_params &p, const int L[4], std::stri
     if (p.stencil_tps != 0 && p.stencil_tps != 1 && p.stencil_tps != 4) { err = "stencil_tps must be 0, 1 or 4"; return OVL_EINVAL; }
     if (p.sap_tps != 0 && p.sap_tps != 1 && p.sap_tps != 2 && p.sap_tps != 4) { err = "sap_tps must be 0, 1, 2 or 4"; return OVL_EINVAL; }
     if (p.adaptive_poles != 0 && p.adaptive_poles != 1) { err = "adaptive_poles must be 0 or 1"; return OVL_EINVAL; }
+    if (p.n_deflate < 0 || p.n_deflate > 48) { err = "n_deflate must be in [0, 48]"; return OVL_EINVAL; }
+    if (p.n_deflate > 0 && !(p.deflate_tol > 0 && p.deflate_tol <= 1e-3)) { err = "deflate_tol must be in (0, 1e-3]"; return OVL_EINVAL; }
     for (int m = 0; m < 4 && p.precond != OVL_PREC_NONE; m++) {
         if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m]) {
             err = "sap_block must be even and divide the lattice extent";
@@ -109,22 +113,6 @@ static bool is_device_ptr(const void *p) {
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
-
-#define CK(expr)                                                                   \
-    do {                                                                           \
-        cudaError_t e_ = (expr);                                                   \
-        if (e_ != cudaSuccess) {                                                   \
-            cudaGetLastError();                                                    \
-            c->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #expr; \
-            return OVL_ECUDA;                                                      \
-        }                                                                          \
-    } while (0)
-
-#define ST(expr)                          \
-    do {                                  \
-        ovl_status s_ = (expr);           \
-        if (s_ != OVL_OK) return s_;      \
-    } while (0)
 
 ovl_status Ctx::alloc(void **p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes);
@@ -360,9 +348,16 @@ ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
     PhaseClock pclk(this, &t_sign64);
     Ctx *c = this;
     ST(ensure_ms64());
+    // with deflation the multishift sees Pi b only; the deflated eigenpairs are added exactly
+    std::vector<double> dc;
+    const double2 *bm = b;
+    if (ndefl) {
+        ST(defl_project64(b, defl_tmp64, dc));
+        bm = defl_tmp64;
+    }
     int n;
     ST(ms_setup(ms64_state, tol, &n));
-    CK(ms_init_f64(g, n, ms64_state, ms64, b, rs, stream));
+    CK(ms_init_f64(g, n, ms64_state, ms64, bm, rs, stream));
     int iters = 0;
     auto fn = [&](cudaEvent_t *e, unsigned f) { return ms_iter_f64(g, U64, m0_ker, ms64_state, ms64, rs, stream, e, f); };
     ST(ms_run(ms64_state, 0, 0, 48.0 * 8.0, fn, &iters));
@@ -370,6 +365,7 @@ ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
     const double sc = zs_d0[n - 1] / lam_min;
     if (mode == 0) CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 1, sc, nullptr, 0.0, stream));
     else CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 0, sc, b, rho, stream));
+    if (ndefl) ST(defl_add64(dc, out, mode));
     return OVL_OK;
 }
 
@@ -379,6 +375,12 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
     Ctx *c = this;
     int iters = 0, n = npole;
     const float4 *y;
+    std::vector<double> dc;
+    const float4 *b_orig = b;
+    if (ndefl) {   // as in sign64: the multishift sees Pi b
+        ST(defl_project32(b, defl_tmp32, dc));
+        b = defl_tmp32;
+    }
     if (p.precision == OVL_MIXED_HALF || p.precision == OVL_MIXED_BF16) {
         // shifted directions stored in 16 bits (per site: 48 B, + 4 B norm for FP16, read and written)
         const bool bf = p.precision == OVL_MIXED_BF16;
@@ -403,7 +405,8 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
     stat_ms32 += iters;
     const float sc = (float)(zs_d0[n - 1] / lam_min);
     if (mode == 0) CK(wilson_f32(g, U32, y, out, (float)m0_ker, 1, sc, nullptr, 0.f, stream));
-    else CK(wilson_f32(g, U32, y, out, (float)m0_ker, 0, sc, b, (float)rho, stream));
+    else CK(wilson_f32(g, U32, y, out, (float)m0_ker, 0, sc, b_orig, (float)rho, stream));
+    if (ndefl) ST(defl_add32(dc, out, mode));
     return OVL_OK;
 }
 
@@ -520,6 +523,12 @@ static double min_positive(const double *tol, int n) {
 
 ovl_status Ctx::sign64_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode) {
     Ctx *c = this;
+    if (ndefl) {   // deflation runs through the single-right-hand-side path
+        const long w = (long)g.V * 12;
+        for (int y = 0; y < nrhs; y++)
+            if (tol[y] > 0) ST(sign64(b + y * w, out + y * w, tol[y], mode));
+        return OVL_OK;
+    }
     ST(ensure_batch());
     if (!msb64.p || msb64_cap < nrhs) {   // sized to the batch (grown when a larger one comes)
         if (msb64.p) {
@@ -551,6 +560,12 @@ ovl_status Ctx::sign64_batch(const double2 *b, double2 *out, int nrhs, const dou
 
 ovl_status Ctx::sign32_batch(const float4 *b, float4 *out, int nrhs, const double *tol, int mode) {
     Ctx *c = this;
+    if (ndefl) {
+        const long w = (long)g.V * 6;
+        for (int y = 0; y < nrhs; y++)
+            if (tol[y] > 0) ST(sign32(b + y * w, out + y * w, tol[y], mode));
+        return OVL_OK;
+    }
     ST(ensure_batch());
     if (!msb32.p || msb32_cap < nrhs) {
         if (msb32.p) {
@@ -1013,6 +1028,10 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
         c->lam_max = 1.05 * lmax;
         c->lam_estimated = true;
     }
+    if (c->p.n_deflate > 0) {   // the rational approximation then starts at 0.9 |lambda_{k+1}|
+        ST(c->deflation_setup());
+        c->lam_min = std::max(c->lam_min, 0.9 * c->defl_next);
+    }
     ST(c->set_zolotarev());
     // preconditioner mass m0^def (Eq. default_m) unless given
     c->sigma_min = NAN;
@@ -1176,6 +1195,28 @@ extern "C" ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, flo
     if (tps32) *tps32 = c->g.tps32;
     if (ms)
         for (int k = 0; k < 4; k++) ms[k] = c->tune_ms[k];
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_hermitian_eig(int n, const double *A, double *w, double *Z) {
+    if (n < 1 || !A || !w || !Z) return OVL_EINVAL;
+    std::vector<std::complex<double>> a((size_t)n * n);
+    for (size_t k = 0; k < (size_t)n * n; k++) a[k] = std::complex<double>(A[2 * k], A[2 * k + 1]);
+    const int r = hermitian_eig(n, a.data(), w, reinterpret_cast<std::complex<double> *>(Z));
+    return r == 0 ? OVL_OK : OVL_ENOCONV;
+}
+
+extern "C" ovl_status ovl_deflation_info(const ovl_ctx *ctx, int *k, double *lambda, double *lambda_next,
+                                         double *setup_s, double *resid_max, long *matvecs) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c) return OVL_EINVAL;
+    if (k) *k = c->ndefl;
+    if (lambda)
+        for (int i = 0; i < c->ndefl; i++) lambda[i] = c->defl_lambda[i];
+    if (lambda_next) *lambda_next = c->defl_next;
+    if (setup_s) *setup_s = c->defl_setup_s;
+    if (resid_max) *resid_max = c->defl_resid;
+    if (matvecs) *matvecs = c->defl_matvecs;
     return OVL_OK;
 }
 

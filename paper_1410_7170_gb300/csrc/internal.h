@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <complex>
 #include <string>
 
 #include "common.cuh"
@@ -221,5 +222,9 @@ void set_thread_error(const std::string &msg);
 
 // ---------------------------------------------------------------- host Zolotarev
 int zolotarev_host(double k, int n, double *d0, double *a, double *c, double *delta);
+
+// Eigenvalues (ascending) and eigenvectors (columns of Z, row-major) of a small complex
+// Hermitian matrix A (row-major, overwritten), by cyclic Jacobi; 0 on convergence.
+int hermitian_eig(int n, std::complex<double> *A, double *w, std::complex<double> *Z);
 
 }  // namespace ovl

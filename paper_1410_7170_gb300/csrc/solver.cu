@@ -23,21 +23,6 @@
 
 namespace ovl {
 
-#define CK(expr)                                                                   \
-    do {                                                                           \
-        cudaError_t e_ = (expr);                                                   \
-        if (e_ != cudaSuccess) {                                                   \
-            cudaGetLastError();                                                    \
-            c->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #expr; \
-            return OVL_ECUDA;                                                      \
-        }                                                                          \
-    } while (0)
-#define ST(expr)                     \
-    do {                             \
-        ovl_status s_ = (expr);      \
-        if (s_ != OVL_OK) return s_; \
-    } while (0)
-
 using cd = std::complex<double>;
 
 template <typename T> struct Ops;

@@ -9,6 +9,25 @@
 
 namespace ovl {
 
+// Status propagation inside Ctx members and helpers (a Ctx *c must be in scope for CK):
+// CK turns a CUDA error into OVL_ECUDA with the failing call recorded in c->err (and the
+// sticky last-error cleared); ST returns any non-OK ovl_status.
+#define CK(expr)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            cudaGetLastError();                                                    \
+            c->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #expr; \
+            return OVL_ECUDA;                                                      \
+        }                                                                          \
+    } while (0)
+#define ST(expr)                     \
+    do {                             \
+        ovl_status s_ = (expr);      \
+        if (s_ != OVL_OK) return s_; \
+    } while (0)
+
+
 struct GraphSlot {
     cudaGraphExec_t exec = nullptr;
     int chunk = 0;
@@ -120,6 +139,15 @@ struct Ctx {
     double t_sign64 = 0, t_sign_low = 0, t_prec = 0;   // phase wall times of the current solve (s)
     bool sap_tuned = false;
     float sap_ms[3] = {0, 0, 0};       // one FP32 Schwarz cycle, ms: 1, 2, 4 threads per site
+    // low-mode deflation of the sign function (params.n_deflate > 0)
+    int ndefl = 0;
+    double2 *defl64 = nullptr, *defl64g5 = nullptr;   // eigenvectors xi_i of Q and gamma5 xi_i (FP64)
+    float4 *defl32 = nullptr, *defl32g5 = nullptr;    // the same in FP32
+    double2 *defl_tmp64 = nullptr;                    // projected right-hand side
+    float4 *defl_tmp32 = nullptr;
+    std::vector<double> defl_lambda;                  // eigenvalues of the deflated pairs (signed)
+    double defl_next = 0, defl_setup_s = 0, defl_resid = 0;   // |lambda_{k+1}|, seconds, max ||Q xi - lambda xi||
+    long defl_matvecs = 0;                            // Q^2 applications of the eigensolver
 
     ~Ctx();
     ovl_status alloc(void **p, size_t bytes);
@@ -152,6 +180,11 @@ struct Ctx {
     ovl_status set_zolotarev();
     ovl_status autotune();
     ovl_status autotune_sap();
+    ovl_status deflation_setup();
+    ovl_status defl_project64(const double2 *b, double2 *bp, std::vector<double> &coef);
+    ovl_status defl_add64(const std::vector<double> &coef, double2 *out, int mode);
+    ovl_status defl_project32(const float4 *b, float4 *bp, std::vector<double> &coef);
+    ovl_status defl_add32(const std::vector<double> &coef, float4 *out, int mode);
 };
 
 // Wall time of a solver phase, added to *acc when the scope ends. With profiling on, the

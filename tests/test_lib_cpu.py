@@ -72,3 +72,24 @@ def test_zolotarev_rejects_bad_interval():
         ovl.ovl_zolotarev(1.5, 10)
     with pytest.raises(ovl.OvlError):
         ovl.ovl_zolotarev(0.1, 0)
+
+
+@pytest.mark.parametrize("n", [1, 3, 17, 96])
+def test_host_hermitian_eig_matches_numpy(n):
+    """The host Jacobi eigensolver (Rayleigh-Ritz steps of the low-mode eigensolver): the
+    eigenvalues agree with LAPACK's, the eigenvectors satisfy A Z = Z diag(w) and are
+    orthonormal."""
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = A + A.conj().T
+    w, Z = ovl.hermitian_eig(A)
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12 * np.abs(w).max()
+    assert np.abs(A @ Z - Z * w).max() < 1e-12 * np.abs(w).max()
+    assert np.abs(Z.conj().T @ Z - np.eye(n)).max() < 1e-13
+
+
+def test_host_hermitian_eig_degenerate_and_diagonal():
+    w, Z = ovl.hermitian_eig(np.diag([3.0, 1.0, 1.0, -2.0]).astype(complex))
+    assert np.allclose(w, [-2.0, 1.0, 1.0, 3.0])
+    with pytest.raises(ovl.OvlError):
+        ovl.hermitian_eig(np.zeros((0, 0), dtype=complex))
