@@ -126,6 +126,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(values, dist, device="cpu"):
+    """Elementwise maximum of per-rank timings (replicas: the job takes as long as its
+    slowest rank); without a process group the values come back unchanged."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the (max-over-ranks) time."""
+    return units_per_rank * world / seconds
+
+
 def make_inputs(rank):
     import synth
     U = synth.gauge_field(DIMS, 0.5, GAUGE_SEED, stout_steps=3, stout_eps=0.1)
@@ -224,10 +239,7 @@ def run_ours(args, rank, world, dist):
     op64.close()
 
     # max over ranks
-    vals = torch.tensor([ms_mixed, e2e_s, ms_64], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_mixed, e2e_s, ms_64 = vals.tolist()
+    ms_mixed, e2e_s, ms_64 = max_over_ranks([ms_mixed, e2e_s, ms_64], dist, dev)
     if rank != 0:
         return None
     pk, pk_kind = peaks()
@@ -254,7 +266,7 @@ def run_ours(args, rank, world, dist):
     spinor_bytes = V * 12 * 16
     out = {
         "metric": METRIC,
-        "value": args.steps * world / (ms_mixed * 1e-3),
+        "value": job_rate(args.steps, world, ms_mixed * 1e-3),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
@@ -269,7 +281,7 @@ def run_ours(args, rank, world, dist):
                    "tol": TOL, "solver": "FGMRES(100) fp64 + inner FGMRES fp32 (Table 3) + Wilson FGMRES fp32",
                    "n_poles": 20, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "fp64_gpu": {"value": fp64_steps * world / (ms_64 * 1e-3), "unit": UNIT, "steps": fp64_steps,
+        "fp64_gpu": {"value": job_rate(fp64_steps, world, ms_64 * 1e-3), "unit": UNIT, "steps": fp64_steps,
                      "warmup": 1, "outer_iters": st_64[-1]["outer_iters"],
                      "ms_iters_fp64": st_64[-1]["ms_iters_fp64"]},
         "mixed_stats": st_mixed[-1],
@@ -293,7 +305,7 @@ def run_ours(args, rank, world, dist):
                      "hbm_peak_gbs": pk["hbm_gbs"],
                      "timing": "CUDA events recorded by the library around the kernels of one multishift "
                                "iteration of every queued chunk of 8, inside the timed region"},
-        "e2e": {"value": e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * spinor_bytes,
+        "e2e": {"value": job_rate(e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 2 * spinor_bytes,
                 "d2h_bytes_per_step": spinor_bytes},
         "gpu_launches": prof["launches"],
         "clocks": clocks,
