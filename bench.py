@@ -15,6 +15,7 @@ import hashlib
 import json
 import os
 import statistics
+import tempfile
 import subprocess
 import sys
 import time
@@ -77,7 +78,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "bench_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
