@@ -481,3 +481,42 @@ def test_gauge_generator_torch_path_matches_numpy():
     a = synth.gauge_field(dims, 0.5, 77, stout_steps=2)
     b = synth.gauge_field(dims, 0.5, 77, stout_steps=2, device="cuda")
     assert np.abs(a - b).max() < 1e-12
+
+
+def test_edge_cases_zero_rhs_and_smallest_lattice():
+    """Degenerate inputs: b = 0 gives x = 0 (and sign(Q) 0 = 0, D_N 0 = 0) without
+    iterating; n_rhs = 0 is an argument error; the smallest lattice 2^4 (16 sites, wrap-around
+    neighbours in every direction) matches the dense oracle for D_W, sign(Q) and the solve."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 1206)
+    op = ovl.Overlap(U, dims, 1.0, 0.05, params())
+    z = torch.zeros((256, 4, 3), dtype=torch.complex128, device="cuda")
+    x = torch.ones_like(z)
+    st, stats = op.ovl_solve(x, z, 1, 1e-10)
+    assert torch.count_nonzero(x).item() == 0 and stats["outer_iters"] == 0
+    out = torch.ones_like(z)
+    op.sign_apply(out, z, 1e-10)
+    assert torch.count_nonzero(out).item() == 0
+    op.ovl_apply(out, z, 1e-10)
+    assert torch.count_nonzero(out).item() == 0
+    with pytest.raises(ovl.OvlError) as e:
+        op.ovl_solve(x, z, 0, 1e-10)
+    assert e.value.status == ovl.OVL_EINVAL
+    op.close()
+    dims = (2, 2, 2, 2)
+    U = synth.gauge_field(dims, 0.3, 1207)
+    rho = dense.rho_from_mu(0.05, -1.0)
+    DN, S, w = dense.overlap_dense(U, dims, rho, -1.0)
+    aw = np.abs(w)
+    op = ovl.Overlap(U, dims, 1.0, 0.05, params(lambda_min=0.98 * aw.min(), lambda_max=1.02 * aw.max()))
+    b = synth.rhs_gaussian(dims, 2207)
+    out = np.empty_like(b)
+    op.wilson_apply(out, b, -1.0)
+    assert relmax(out, sparse.wilson(b, U, dims, -1.0)) < 1e-13
+    o = torch.empty_like(dev(b))
+    op.sign_apply(o, dev(b), 1e-12)
+    assert rel2(host(o), (S @ b.reshape(-1)).reshape(b.shape)) < 1e-10
+    x = torch.zeros_like(dev(b))
+    op.ovl_solve(x, dev(b), 1, 1e-11)
+    assert rel2(host(x), dense.overlap_solve_dense(DN, b)) < 1e-8
+    op.close()
