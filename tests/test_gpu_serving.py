@@ -116,3 +116,40 @@ def test_budget_admission_and_host_side_faults():
     srv.close()
     for x in xs:
         assert np.all(np.isfinite(x)) and np.linalg.norm(x) > 0
+
+
+def test_serving_full_size_range():
+    """The serving configuration's size range: lattices 8^4 to 32^4 and 1 to 12 right-hand
+    sides arrive together on 2 slots (the 32^4 gauge field is generated on the device). Every
+    request completes, and every served solution meets the tolerance in the true FP64 residual
+    of the library's own D_N."""
+    specs = [((8, 8, 8, 8), 12, 0.05), ((24, 24, 24, 24), 2, 0.01), ((32, 32, 32, 32), 1, 0.02),
+             ((16, 16, 16, 16), 4, 0.1), ((24, 24, 24, 24), 1, 0.05)]
+    gauges = {}
+    for i, (d, nr, mu) in enumerate(specs):
+        if d not in gauges:
+            dev = "cuda" if d[0] >= 24 else None
+            gauges[d] = synth.gauge_field(d, 0.5, 950 + i, stout_steps=3, device=dev)
+    p = _params()
+    srv = ovl.Server(slots=2)
+    tickets, outs, bs = [], [], []
+    for k, (d, nr, mu) in enumerate(specs):
+        b = torch.from_numpy(synth.rhs_gaussian(d, 6000 + k, n_rhs=nr)).cuda()
+        x = torch.zeros_like(b)
+        bs.append(b)
+        outs.append(x)
+        tickets.append(srv.submit(torch.from_numpy(gauges[d]).cuda(), d, 1.0, mu, b, x, nr, TOL, p,
+                                  gauge_key=100 + list(gauges).index(d)))
+    results = [srv.wait(t) for t in tickets]
+    rep = srv.report()
+    srv.close()
+    assert rep["completed"] == len(specs) and rep["failed"] == 0, rep
+    for (d, nr, mu), b, x, res in zip(specs, bs, outs, results):
+        assert res["status"] == ovl.OVL_OK, res["message"]
+        op = ovl.Overlap(torch.from_numpy(gauges[d]).cuda(), d, 1.0, mu, ovl.params_default())
+        for k in range(nr):
+            ax = torch.empty_like(x[k])
+            op.ovl_apply(ax, x[k].contiguous(), 1e-12)
+            rel = ((b[k] - ax).norm() / b[k].norm()).item()
+            assert rel < 1.5 * TOL, (d, nr, mu, k, rel)
+        op.close()
