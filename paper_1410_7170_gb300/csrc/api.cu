@@ -55,7 +55,7 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->sap_mr_iters = 6;
     p->prec_restart = 32;
     p->prec_max_iter = 64;
-    p->rhs_block = 1;
+    p->rhs_block = 4;
     p->use_graphs = 1;
     p->check_every = 8;
     p->stencil_tps = 0;
