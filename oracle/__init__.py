@@ -18,9 +18,12 @@ paper defines:
                    and sign(Q) by one plain CG per Zolotarev pole
   * solvers.py     textbook restarted GMRES(m) and right-preconditioned
                    FGMRES(m) (Sec. 5.1)
+  * krylov_sign.py the restarted Krylov sign function of Sec. 5.2
+                   (quadrature-based restarts, optional thick restarts)
 
 Every function is pinned by tests against closed forms, invariants or
 library routines (free-field spectrum, Gamma5-hermiticity, sign^2 = I,
 Ginsparg-Wilson, normality, gauge covariance, Prop. Fnorm, the alternation
-theorem for the Zolotarev coefficients, an SVD polar factor for sign(Q)).
+theorem for the Zolotarev coefficients, an SVD polar factor for sign(Q), the
+closed form of restarted Arnoldi for matrix functions).
 """
