@@ -312,9 +312,58 @@ def run_ours(args, rank, world, dist):
         "clocks": clocks,
     }
     out["dslash"] = dslash(ovl, torch, dev, pk["hbm_gbs"])
+    out["sign_methods"] = sign_methods(ovl, torch, U, b, dev, stream, info)
     out["serving"] = serving(ovl, torch, dev)
     out["cpu_baseline"] = cpu_baseline(st_64[-1], budget_s=args.cpu_budget)
     return out
+
+
+def sign_methods(ovl, torch, U, b, dev, stream, info, tol=1e-10, reps=3):
+    """One FP64 sign(Q) b at tol on the workload's field: Zolotarev + multishift CG against the
+    restarted Krylov method with thick restarts (krylov_m 40, 8 kept Ritz vectors), both on the
+    same spectral interval. Reported: ms per application (CUDA events, L2 flushed before each),
+    products with Q^2 per application and the relative difference of the two results."""
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    b_d = torch.from_numpy(b).to(dev)
+    res, outs = {}, {}
+    for name, method in (("zolotarev_multishift", ovl.OVL_SIGN_ZOLOTAREV), ("krylov_thick_restart", ovl.OVL_SIGN_KRYLOV)):
+        p = ovl.params_default(sign_method=method, krylov_m=40, krylov_keep=8, lambda_min=info["lambda_min"],
+                               lambda_max=info["lambda_max"])
+        op = ovl.Overlap(torch.from_numpy(U).to(dev), DIMS, 1.0, 0.01, p, stream=stream.cuda_stream)
+        out = torch.empty_like(b_d)
+        with torch.cuda.stream(stream):
+            op.sign_apply(out, b_d, tol)                      # warm-up (workspace allocation)
+        torch.cuda.synchronize()
+        k0 = op.krylov_sign_info()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        with torch.cuda.stream(stream):
+            for k in range(reps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                op.sign_apply(out, b_d, tol)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(e) for a, e in ev) / reps
+        k1 = op.krylov_sign_info()
+        if method == ovl.OVL_SIGN_ZOLOTAREV:
+            op.prof_enable(True)
+            op.prof_get(reset=True)
+            with torch.cuda.stream(stream):
+                op.sign_apply(out, b_d, tol)
+            torch.cuda.synchronize()
+            products = op.prof_get(reset=True)["ms_stencil_f64"]["launches"]   # one Q^2 per iteration
+            op.prof_enable(False)
+        else:
+            products = (k1["matvecs"] - k0["matvecs"]) / reps
+        res[name] = {"ms": ms, "q2_products": products}
+        if method == ovl.OVL_SIGN_KRYLOV:
+            res[name]["cycles"] = (k1["cycles"] - k0["cycles"]) / reps
+        outs[name] = out.clone()
+        op.close()
+    a, c = outs["zolotarev_multishift"], outs["krylov_thick_restart"]
+    res["rel_diff"] = ((a - c).norm() / a.norm()).item()
+    res["tol"] = tol
+    return res
 
 
 def dslash(ovl, torch, dev, hbm_gbs, dims=(64, 32, 32, 32)):

@@ -70,6 +70,11 @@ typedef enum {
                                preconditioned by the inexact Wilson solve (Sec. 5.3) */
 } ovl_precond;
 
+typedef enum {
+    OVL_SIGN_ZOLOTAREV = 0, /* Zolotarev rational approximation evaluated by multishift CG */
+    OVL_SIGN_KRYLOV = 1     /* restarted Krylov method with thick restarts (Sec. 5.2, FP64 only) */
+} ovl_sign_method;
+
 /* Solver and approximation parameters. Defaults (ovl_params_default) are the
  * paper's Table 2 / Table 3 values where the paper gives one. */
 typedef struct {
@@ -111,13 +116,24 @@ typedef struct {
                                interval starts at 0.9 |lambda_{k+1}|. 0 (default): no deflation; <= 48 */
     double deflate_tol;     /* eigenpair accuracy: Ritz residual of Q^2 <= deflate_tol * lambda_max^2
                                (default 1e-13) */
+    int sign_method;        /* ovl_sign_method of every FP64 sign application (sign_apply, ovl_apply, the
+                               outer D_N of ovl_solve); FP32/FP16/BF16 inner applications always use
+                               Zolotarev. Default OVL_SIGN_ZOLOTAREV. OVL_SIGN_KRYLOV computes
+                               sign(Q) b = (Q^2)^{-1/2} Q b by restarted Lanczos on Q^2 with
+                               quadrature-based restarts (the integral (2/pi) int ds/(Q^2 + s^2)
+                               by the trapezoidal rule in ln s) and stops when its error bound
+                               (from lambda_min) is <= tol ||b||; right-hand sides run one at a time */
+    int krylov_m;           /* basis vectors per cycle of the Krylov sign (4..120; default 40) */
+    int krylov_keep;        /* Ritz vectors of the smallest Ritz values of Q^2 kept at a restart
+                               (thick restart; 0 = plain restart; <= krylov_m - 2; default 8) */
 } ovl_params;
 
 /* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
 typedef struct {
     int outer_iters;        /* outer (F)GMRES iterations, summed over right-hand sides */
     int inner_iters;        /* inner FGMRES iterations (recursive mode) */
-    long ms_iters_fp64;     /* multishift CG iterations in FP64 sign applications */
+    long ms_iters_fp64;     /* multishift CG iterations in FP64 sign applications (with
+                               OVL_SIGN_KRYLOV: its products with Q^2) */
     long ms_iters_low;      /* multishift CG iterations in FP32/FP16 sign applications */
     long prec_iters;        /* Wilson FGMRES iterations inside the preconditioner */
     double true_rel_resid;  /* max over RHS of ||b - D_N x|| / ||b||, recomputed in FP64 at exit */
@@ -170,12 +186,18 @@ ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, float *ms);
 ovl_status ovl_deflation_info(const ovl_ctx *ctx, int *k, double *lambda, double *lambda_next, double *setup_s,
                               double *resid_max, long *matvecs);
 
+/* Restarted Krylov sign function totals since ovl_create: cycles and products with Q^2
+ * (nullable outputs). Zero while params.sign_method is OVL_SIGN_ZOLOTAREV. */
+ovl_status ovl_krylov_sign_info(const ovl_ctx *ctx, long *cycles, long *matvecs);
+
 /* Host utility: eigenvalues w[n] (ascending) and eigenvectors Z (n x n complex, row-major,
  * column j for w[j]) of the n x n complex Hermitian matrix A (row-major, interleaved re/im,
- * 2 n^2 doubles; not modified), by cyclic Jacobi rotations. The library uses it for the
- * Rayleigh-Ritz steps of the low-mode eigensolver (an implementation choice; the paper
- * computes its eigenpairs with PARPACK). OVL_EINVAL for n < 1 or NULL pointers, OVL_ENOCONV
- * if 100 sweeps do not converge. */
+ * 2 n^2 doubles; not modified), by Householder reduction to real tridiagonal form and
+ * implicit symmetric QR steps with Wilkinson shifts (Golub and Van Loan, Sec. 8.3). The
+ * library uses it for the Rayleigh-Ritz steps of the low-mode eigensolver and of the
+ * Krylov sign function (an implementation choice; the paper computes its eigenpairs with
+ * PARPACK). OVL_EINVAL for n < 1 or NULL pointers, OVL_ENOCONV if the QR iteration takes
+ * more than 60 n + 100 steps. */
 ovl_status ovl_hermitian_eig(int n, const double *A, double *w, double *Z);
 
 /* Threads per block site chosen for the FP32 Schwarz block solves of the Wilson

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libovl.so")
 OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ENOCONV, OVL_EBREAKDOWN, OVL_ETIMEOUT, OVL_ECUDA = range(7)
 OVL_FP64, OVL_MIXED_FP32, OVL_MIXED_HALF, OVL_MIXED_BF16 = range(4)
 OVL_PREC_NONE, OVL_PREC_WILSON, OVL_PREC_RECURSIVE = range(3)
+OVL_SIGN_ZOLOTAREV, OVL_SIGN_KRYLOV = range(2)
 _STATUS = {0: "OVL_OK", 1: "OVL_EINVAL", 2: "OVL_ENOMEM", 3: "OVL_ENOCONV", 4: "OVL_EBREAKDOWN",
            5: "OVL_ETIMEOUT", 6: "OVL_ECUDA"}
 
@@ -41,7 +42,8 @@ class ovl_params(ctypes.Structure):
         ("prec_restart", ctypes.c_int), ("prec_max_iter", ctypes.c_int), ("rhs_block", ctypes.c_int),
         ("use_graphs", ctypes.c_int), ("check_every", ctypes.c_int), ("stencil_tps", ctypes.c_int),
         ("sap_tps", ctypes.c_int), ("adaptive_poles", ctypes.c_int), ("n_deflate", ctypes.c_int),
-        ("deflate_tol", ctypes.c_double),
+        ("deflate_tol", ctypes.c_double), ("sign_method", ctypes.c_int), ("krylov_m", ctypes.c_int),
+        ("krylov_keep", ctypes.c_int),
     ]
 
 
@@ -96,7 +98,7 @@ class ovl_prof(ctypes.Structure):
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
-           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
+           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
            "ovl_apply_n", "ovl_dslash_time_n", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
@@ -130,6 +132,7 @@ def lib():
         L.ovl_hermitian_eig.argtypes = [I_, P, P, P]
         L.ovl_deflation_info.argtypes = [P, ctypes.POINTER(I_), P, ctypes.POINTER(D), ctypes.POINTER(D),
                                          ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
+        L.ovl_krylov_sign_info.argtypes = [P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]
         L.wilson_apply_noalloc.argtypes = [P, P, P, P, D, I_, P]
         L.ovl_dslash_time.argtypes = [P, I_, I_, ctypes.POINTER(D)]
         L.wilson_apply_n.argtypes = [P, P, P, I_, D]
@@ -282,6 +285,12 @@ def ovl_deflation_info(ctx):
             "resid_max": res.value, "matvecs": mv.value}
 
 
+def ovl_krylov_sign_info(ctx):
+    cyc, mv = ctypes.c_long(), ctypes.c_long()
+    _check(lib().ovl_krylov_sign_info(ctx, ctypes.byref(cyc), ctypes.byref(mv)), ctx)
+    return {"cycles": cyc.value, "matvecs": mv.value}
+
+
 def ovl_tuning_sap(ctx):
     import numpy as np
     a = ctypes.c_int()
@@ -375,6 +384,9 @@ class Overlap:
 
     def deflation_info(self):
         return ovl_deflation_info(self.ctx)
+
+    def krylov_sign_info(self):
+        return ovl_krylov_sign_info(self.ctx)
 
     def dslash_time(self, precision, reps=20):
         return ovl_dslash_time(self.ctx, precision, reps)

@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libovl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["dslash.cu", "blas.cu", "multishift.cu", "solver.cu", "api.cu", "sap.cu", "multirhs.cu", "deflate.cu",
-              "noalloc.cu", "server.cu"]
+              "krylov.cu", "noalloc.cu", "server.cu"]
 CXX_SOURCES = ["zolotarev.cpp", "eig_host.cpp"]
 
 
@@ -56,7 +56,7 @@ def build(force=False, verbose=False):
     for s in cxx:
         src = os.path.join(CSRC, s)
         obj = os.path.join(OUT_DIR, s + ".o")
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-c", src, "-o", obj]
+        cmd = ["g++", "-O2", "-fcx-limited-range", "-std=c++17", "-fPIC", "-c", src, "-o", obj]
         jobs.append((obj, src, cmd))
     todo = [(o, c) for o, s, c in jobs if force or _stale(o, [s] + headers)]
 

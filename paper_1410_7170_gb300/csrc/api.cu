@@ -63,6 +63,9 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->adaptive_poles = 1;
     p->n_deflate = 0;
     p->deflate_tol = 1e-13;
+    p->sign_method = OVL_SIGN_ZOLOTAREV;
+    p->krylov_m = 40;
+    p->krylov_keep = 8;
     return OVL_OK;
 }
 
@@ -90,6 +93,9 @@ static ovl_status validate_params(const ovl_params &p, const int L[4], std::stri
     if (p.adaptive_poles != 0 && p.adaptive_poles != 1) { err = "adaptive_poles must be 0 or 1"; return OVL_EINVAL; }
     if (p.n_deflate < 0 || p.n_deflate > 48) { err = "n_deflate must be in [0, 48]"; return OVL_EINVAL; }
     if (p.n_deflate > 0 && !(p.deflate_tol > 0 && p.deflate_tol <= 1e-3)) { err = "deflate_tol must be in (0, 1e-3]"; return OVL_EINVAL; }
+    if (p.sign_method != OVL_SIGN_ZOLOTAREV && p.sign_method != OVL_SIGN_KRYLOV) { err = "sign_method must be 0 or 1"; return OVL_EINVAL; }
+    if (p.krylov_m < 4 || p.krylov_m > 120) { err = "krylov_m must be in [4,120]"; return OVL_EINVAL; }
+    if (p.krylov_keep < 0 || p.krylov_keep > p.krylov_m - 2) { err = "krylov_keep must be in [0, krylov_m - 2]"; return OVL_EINVAL; }
     for (int m = 0; m < 4 && p.precond != OVL_PREC_NONE; m++) {
         if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m]) {
             err = "sap_block must be even and divide the lattice extent";
@@ -345,6 +351,7 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes
 //   mode 0: out = (d0/lmin) gamma5 D_W y = sign(Q) b
 //   mode 1: out = rho b + (d0/lmin) D_W y   = D_N b
 ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
+    if (p.sign_method == OVL_SIGN_KRYLOV) return sign64_krylov(b, out, tol, mode);
     PhaseClock pclk(this, &t_sign64);
     Ctx *c = this;
     ST(ensure_ms64());
@@ -523,7 +530,7 @@ static double min_positive(const double *tol, int n) {
 
 ovl_status Ctx::sign64_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode) {
     Ctx *c = this;
-    if (ndefl) {   // deflation runs through the single-right-hand-side path
+    if (ndefl || p.sign_method == OVL_SIGN_KRYLOV) {   // deflation and the Krylov sign run one at a time
         const long w = (long)g.V * 12;
         for (int y = 0; y < nrhs; y++)
             if (tol[y] > 0) ST(sign64(b + y * w, out + y * w, tol[y], mode));
@@ -1217,6 +1224,14 @@ extern "C" ovl_status ovl_deflation_info(const ovl_ctx *ctx, int *k, double *lam
     if (setup_s) *setup_s = c->defl_setup_s;
     if (resid_max) *resid_max = c->defl_resid;
     if (matvecs) *matvecs = c->defl_matvecs;
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_krylov_sign_info(const ovl_ctx *ctx, long *cycles, long *matvecs) {
+    if (!ctx) return OVL_EINVAL;
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (cycles) *cycles = c->ks_cycles;
+    if (matvecs) *matvecs = c->ks_matvecs;
     return OVL_OK;
 }
 

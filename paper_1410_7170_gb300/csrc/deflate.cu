@@ -12,7 +12,7 @@
 // with two-pass classical Gram-Schmidt against the whole basis (so the projected matrix is
 // formed from the orthogonalisation coefficients and stays Hermitian to rounding):
 //   extend the basis to m vectors; Rayleigh-Ritz on the m x m projected matrix (host
-//   Jacobi); a Ritz pair (theta, V s) has residual norm |beta_m s_m|; keep the nkeep
+//   eigensolver); a Ritz pair (theta, V s) has residual norm |beta_m s_m|; keep the nkeep
 //   smallest Ritz vectors plus the last basis vector (the projected matrix becomes
 //   diag(theta) bordered by beta_m s_m) and extend again, until k + 1 pairs converge.
 // A final Rayleigh-Ritz step with Q itself on the converged vectors gives the signed

@@ -1,13 +1,20 @@
-// Eigen-decomposition of a small complex Hermitian matrix on the host (cyclic Jacobi).
+// Eigen-decomposition of a small complex Hermitian matrix on the host, for the Rayleigh-Ritz
+// steps of the low-mode eigensolver and of the restarted Krylov sign function (orders up to
+// ~120, once per restart cycle).
 //
-// Each step annihilates one off-diagonal pair (p, q). With a_pq = |a_pq| e^{i phi},
-// tau = (a_qq - a_pp) / (2 |a_pq|) and t = sgn(tau) / (|tau| + sqrt(1 + tau^2)) (the
-// smaller root of t^2 + 2 tau t - 1 = 0), c = 1 / sqrt(1 + t^2), s = t c, the unitary
-//   R = [[c, s e^{i phi}], [-s e^{-i phi}, c]]   (acting on coordinates p, q)
-// makes (R^H A R)_pq = e^{i phi} (|a_pq| (c^2 - s^2) + c s (a_pp - a_qq)) = 0. Sweeps over
-// all pairs repeat until the off-diagonal part is below 1e-15 of the matrix norm; the
-// accumulated product of the R is the matrix of eigenvectors. Used for the Rayleigh-Ritz
-// steps of the low-mode eigensolver (matrices of order <= a few hundred).
+// 1. Householder reduction to tridiagonal form (Golub and Van Loan, Matrix Computations,
+//    Sec. 8.3.1): for column k the reflector H = I - 2 v v^H maps A[k+1:, k] onto
+//    -phi alpha e_1 (alpha its norm, phi the phase of its first entry); the trailing block
+//    becomes B - 2 v q^H - 2 q v^H with p = B v, K = v^H p, q = p - K v. The reflectors
+//    accumulate into Q (A = Q T Q^H).
+// 2. A diagonal unitary D (d_0 = 1, d_{i+1} = d_i s_i/|s_i| for the subdiagonal s_i) makes
+//    T real: D^H T D has subdiagonal |s_i|, and Q D carries the phases.
+// 3. Implicit symmetric QR steps with the Wilkinson shift (ibid., Sec. 8.3.3) on the
+//    unreduced blocks of the real tridiagonal matrix, chasing the bulge with Givens
+//    rotations that are applied to the columns of Q D. A subdiagonal entry is set to zero
+//    once it is below 2^-52 (|d_i| + |d_{i+1}|).
+// Eigenvalues are returned in ascending order with their eigenvectors.
+#include <float.h>
 #include <math.h>
 
 #include <algorithm>
@@ -22,59 +29,106 @@ using cdh = std::complex<double>;
 // A: n x n Hermitian, row-major (overwritten). w: eigenvalues ascending; Z: n x n row-major,
 // column j the eigenvector of w[j]. Returns 0 on convergence, 1 otherwise.
 int hermitian_eig(int n, cdh *A, double *w, cdh *Z) {
-    std::vector<cdh> V((size_t)n * n, cdh(0));
-    for (int i = 0; i < n; i++) V[(size_t)i * n + i] = 1.0;
-    auto at = [&](int i, int j) -> cdh & { return A[(size_t)i * n + j]; };
-    double fro = 0.0;
-    for (long k = 0; k < (long)n * n; k++) fro += std::norm(A[k]);
-    fro = sqrt(fro);
-    int converged = 0;
-    for (int sweep = 0; sweep < 100; sweep++) {
-        double off = 0.0;
-        for (int i = 0; i < n; i++)
-            for (int j = i + 1; j < n; j++) off += std::norm(at(i, j));
-        if (sqrt(2.0 * off) <= 1e-15 * fro || fro == 0.0) {
-            converged = 1;
+    auto a = [&](int i, int j) -> cdh & { return A[(size_t)i * n + j]; };
+    std::vector<cdh> Q((size_t)n * n, cdh(0)), v(n), p(n);
+    auto q = [&](int i, int j) -> cdh & { return Q[(size_t)i * n + j]; };
+    for (int i = 0; i < n; i++) q(i, i) = 1.0;
+    // 1. Householder tridiagonalisation
+    for (int k = 0; k + 2 < n; k++) {
+        const int r = n - k - 1;   // trailing block A[k+1:, k+1:]
+        double alpha2 = 0.0;
+        for (int i = 0; i < r; i++) alpha2 += std::norm(a(k + 1 + i, k));
+        const double alpha = sqrt(alpha2);
+        if (alpha == 0.0) continue;
+        const cdh x0 = a(k + 1, k);
+        const double ax0 = std::abs(x0);
+        const cdh phi = ax0 > 0.0 ? x0 / ax0 : cdh(1.0);
+        const double vnorm = sqrt(2.0 * alpha * (alpha + ax0));
+        for (int i = 0; i < r; i++) v[i] = a(k + 1 + i, k) / vnorm;
+        v[0] += phi * alpha / vnorm;
+        cdh K(0.0);
+        for (int i = 0; i < r; i++) {
+            cdh s(0.0);
+            for (int j = 0; j < r; j++) s += a(k + 1 + i, k + 1 + j) * v[j];
+            p[i] = s;
+            K += std::conj(v[i]) * s;
+        }
+        const double Kr = K.real();
+        for (int i = 0; i < r; i++) p[i] -= Kr * v[i];   // q = p - K v
+        for (int i = 0; i < r; i++)
+            for (int j = 0; j < r; j++)
+                a(k + 1 + i, k + 1 + j) -= 2.0 * (v[i] * std::conj(p[j]) + p[i] * std::conj(v[j]));
+        a(k + 1, k) = -phi * alpha;
+        a(k, k + 1) = std::conj(a(k + 1, k));
+        for (int i = 1; i < r; i++) a(k + 1 + i, k) = a(k, k + 1 + i) = 0.0;
+        for (int i = 0; i < n; i++) {   // Q <- Q H on columns k+1..n-1
+            cdh y(0.0);
+            for (int j = 0; j < r; j++) y += q(i, k + 1 + j) * v[j];
+            for (int j = 0; j < r; j++) q(i, k + 1 + j) -= 2.0 * y * std::conj(v[j]);
+        }
+    }
+    // 2. real tridiagonal form: diagonal d, subdiagonal e (e[i] couples i and i+1)
+    std::vector<double> d(n), e(std::max(n - 1, 1), 0.0);
+    cdh delta(1.0);
+    for (int i = 0; i < n; i++) {
+        d[i] = a(i, i).real();
+        if (i) for (int r = 0; r < n; r++) q(r, i) *= delta;
+        if (i + 1 < n) {
+            const cdh s = a(i + 1, i);
+            const double as = std::abs(s);
+            e[i] = as;
+            if (as > 0.0) delta *= s / as;
+        }
+    }
+    // 3. implicit symmetric QR with Wilkinson shifts
+    int converged = 1;
+    long steps = 0;
+    const long max_steps = 60L * n + 100;
+    int hi = n - 1;
+    while (hi > 0) {
+        // deflate negligible subdiagonal entries, find the unreduced block [lo, hi]
+        for (int i = 0; i < hi; i++)
+            if (fabs(e[i]) <= DBL_EPSILON * (fabs(d[i]) + fabs(d[i + 1])) || fabs(e[i]) < DBL_MIN) e[i] = 0.0;
+        while (hi > 0 && e[hi - 1] == 0.0) hi--;
+        if (hi == 0) break;
+        int lo = hi - 1;
+        while (lo > 0 && e[lo - 1] != 0.0) lo--;
+        if (++steps > max_steps) {
+            converged = 0;
             break;
         }
-        for (int p = 0; p < n; p++)
-            for (int q = p + 1; q < n; q++) {
-                const double b = std::abs(at(p, q));
-                if (b == 0.0) continue;
-                const cdh ph = at(p, q) / b;   // e^{i phi}
-                const double tau = (at(q, q).real() - at(p, p).real()) / (2.0 * b);
-                const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                const cdh rpq = s * ph, rqp = -s * std::conj(ph);   // R_pq, R_qp; R_pp = R_qq = c
-                // A <- A R (columns p, q)
-                for (int i = 0; i < n; i++) {
-                    const cdh ap = at(i, p), aq = at(i, q);
-                    at(i, p) = ap * c + aq * rqp;
-                    at(i, q) = ap * rpq + aq * c;
-                }
-                // A <- R^H A (rows p, q)
-                for (int j = 0; j < n; j++) {
-                    const cdh ap = at(p, j), aq = at(q, j);
-                    at(p, j) = c * ap + std::conj(rqp) * aq;
-                    at(q, j) = std::conj(rpq) * ap + c * aq;
-                }
-                at(p, q) = 0.0;
-                at(q, p) = 0.0;
-                at(p, p) = at(p, p).real();
-                at(q, q) = at(q, q).real();
-                for (int i = 0; i < n; i++) {
-                    const cdh vp = V[(size_t)i * n + p], vq = V[(size_t)i * n + q];
-                    V[(size_t)i * n + p] = vp * c + vq * rqp;
-                    V[(size_t)i * n + q] = vp * rpq + vq * c;
-                }
+        const double dd = 0.5 * (d[hi - 1] - d[hi]), b = e[hi - 1];
+        const double mu = d[hi] - b * b / (dd + (dd >= 0.0 ? 1.0 : -1.0) * hypot(dd, b));
+        double x = d[lo] - mu, z = e[lo], bulge = 0.0;
+        for (int k = lo; k < hi; k++) {
+            if (k > lo) {
+                x = e[k - 1];
+                z = bulge;
             }
+            const double rr = hypot(x, z);
+            const double c = rr > 0.0 ? x / rr : 1.0, s = rr > 0.0 ? -z / rr : 0.0;
+            if (k > lo) e[k - 1] = rr;
+            const double ak = d[k], bk = d[k + 1], tk = e[k];
+            d[k] = c * c * ak - 2.0 * c * s * tk + s * s * bk;
+            d[k + 1] = s * s * ak + 2.0 * c * s * tk + c * c * bk;
+            e[k] = c * s * (ak - bk) + (c * c - s * s) * tk;
+            if (k + 1 < hi) {
+                bulge = -s * e[k + 1];
+                e[k + 1] *= c;
+            }
+            for (int r = 0; r < n; r++) {   // Q D <- Q D G on columns k, k+1
+                const cdh zk = q(r, k), zk1 = q(r, k + 1);
+                q(r, k) = c * zk - s * zk1;
+                q(r, k + 1) = s * zk + c * zk1;
+            }
+        }
     }
     std::vector<int> idx(n);
     std::iota(idx.begin(), idx.end(), 0);
-    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return at(a, a).real() < at(b, b).real(); });
+    std::sort(idx.begin(), idx.end(), [&](int x, int y) { return d[x] < d[y]; });
     for (int j = 0; j < n; j++) {
-        w[j] = at(idx[j], idx[j]).real();
-        for (int i = 0; i < n; i++) Z[(size_t)i * n + j] = V[(size_t)i * n + idx[j]];
+        w[j] = d[idx[j]];
+        for (int i = 0; i < n; i++) Z[(size_t)i * n + j] = q(i, idx[j]);
     }
     return converged ? 0 : 1;
 }

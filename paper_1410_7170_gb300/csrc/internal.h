@@ -224,7 +224,7 @@ void set_thread_error(const std::string &msg);
 int zolotarev_host(double k, int n, double *d0, double *a, double *c, double *delta);
 
 // Eigenvalues (ascending) and eigenvectors (columns of Z, row-major) of a small complex
-// Hermitian matrix A (row-major, overwritten), by cyclic Jacobi; 0 on convergence.
+// Hermitian matrix A (row-major, overwritten), by Householder tridiagonalisation and implicit QR; 0 on convergence.
 int hermitian_eig(int n, std::complex<double> *A, double *w, std::complex<double> *Z);
 
 }  // namespace ovl

@@ -106,8 +106,7 @@ struct KrylovResult {
     bool converged = false;
 };
 
-// Upload complex coefficients (interleaved) to the device coefficient buffer.
-static ovl_status upload_coef(Ctx *c, const std::vector<cd> &v) {
+ovl_status upload_coef(Ctx *c, const std::vector<cd> &v) {
     double *h = c->h_scal + kScal / 2;
     for (size_t k = 0; k < v.size(); k++) {
         h[2 * k] = v[k].real();

@@ -1,6 +1,7 @@
 // Library context and the host-side solver interfaces (internal).
 #pragma once
 #include <chrono>
+#include <complex>
 #include <string>
 #include <vector>
 
@@ -148,6 +149,11 @@ struct Ctx {
     std::vector<double> defl_lambda;                  // eigenvalues of the deflated pairs (signed)
     double defl_next = 0, defl_setup_s = 0, defl_resid = 0;   // |lambda_{k+1}|, seconds, max ||Q xi - lambda xi||
     long defl_matvecs = 0;                            // Q^2 applications of the eigensolver
+    // restarted Krylov sign function (params.sign_method == OVL_SIGN_KRYLOV)
+    double2 *ks_W = nullptr, *ks_Y = nullptr;         // basis (krylov_m + 1 vectors), kept Ritz vectors
+    double2 *ks_f = nullptr, *ks_tmp = nullptr;       // accumulated f(Q^2) Q b, stencil scratch
+    double *ks_S = nullptr;                           // Ritz coefficients (device)
+    long ks_cycles = 0, ks_matvecs = 0;               // totals since creation
 
     ~Ctx();
     ovl_status alloc(void **p, size_t bytes);
@@ -166,6 +172,8 @@ struct Ctx {
     ovl_status ms_run(MsState *d_state, int which, int slot, double shift_bytes, Iter iter_fn, int *iters_out);
     ovl_status sign64(const double2 *b, double2 *out, double tol, int mode);
     ovl_status sign32(const float4 *b, float4 *out, double tol, int mode);
+    ovl_status sign64_krylov(const double2 *b, double2 *out, double tol, int mode);
+    ovl_status ensure_ksign();
     ovl_status ensure_ms64();
     ovl_status ensure_ms32();
     ovl_status ensure_msh();
@@ -199,6 +207,10 @@ struct PhaseClock {
         *acc += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
 };
+
+// Complex coefficients (interleaved) to c->d_coef through the pinned staging area; the
+// caller makes sure the previous upload has completed (a fetch in between synchronises).
+ovl_status upload_coef(Ctx *c, const std::vector<std::complex<double>> &v);
 
 ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats);
 // Lock-step batched solve of nrhs <= kMaxBatch systems on internal FP64 vectors.

@@ -76,7 +76,7 @@ def test_zolotarev_rejects_bad_interval():
 
 @pytest.mark.parametrize("n", [1, 3, 17, 96])
 def test_host_hermitian_eig_matches_numpy(n):
-    """The host Jacobi eigensolver (Rayleigh-Ritz steps of the low-mode eigensolver): the
+    """The host eigensolver (Rayleigh-Ritz steps of the low-mode eigensolver): the
     eigenvalues agree with LAPACK's, the eigenvectors satisfy A Z = Z diag(w) and are
     orthonormal."""
     rng = np.random.default_rng(n)
@@ -86,6 +86,43 @@ def test_host_hermitian_eig_matches_numpy(n):
     assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12 * np.abs(w).max()
     assert np.abs(A @ Z - Z * w).max() < 1e-12 * np.abs(w).max()
     assert np.abs(Z.conj().T @ Z - np.eye(n)).max() < 1e-13
+
+
+def _eig_ok(A, tol=1e-13):
+    w, Z = ovl.hermitian_eig(A)
+    n = A.shape[0]
+    sc = max(np.abs(w).max(), 1e-300)
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() <= tol * sc * 10
+    assert np.abs(A @ Z - Z * w).max() <= tol * sc * 10
+    assert np.abs(Z.conj().T @ Z - np.eye(n)).max() <= tol * 10
+    assert np.all(np.diff(w) >= 0)
+
+
+def test_host_hermitian_eig_structured_cases():
+    """Shapes the solvers produce: the thick-restart projected matrix (diagonal block of
+    kept Ritz values, bordered by one complex row and column, then tridiagonal), clustered
+    and repeated eigenvalues, a graded spectrum over 13 decades, a tridiagonal matrix whose
+    couplings underflow, 2 x 2, and the zero matrix."""
+    rng = np.random.default_rng(11)
+    n, kk = 40, 8
+    H = np.zeros((n, n), complex)
+    H[np.arange(kk), np.arange(kk)] = rng.uniform(0.3, 1.0, kk)
+    H[kk, :kk] = rng.normal(size=kk) + 1j * rng.normal(size=kk)
+    H[:kk, kk] = H[kk, :kk].conj()
+    for j in range(kk, n):
+        H[j, j] = rng.uniform(1.0, 50.0)
+    for j in range(kk, n - 1):
+        H[j + 1, j] = H[j, j + 1] = rng.uniform(0.1, 5.0)
+    _eig_ok(H)
+    W, _ = np.linalg.qr(rng.normal(size=(30, 30)) + 1j * rng.normal(size=(30, 30)))
+    _eig_ok((W * np.repeat([1.0, 1.0 + 1e-12, 2.0, 5.0, -3.0], 6)) @ W.conj().T)
+    W, _ = np.linalg.qr(rng.normal(size=(25, 25)) + 1j * rng.normal(size=(25, 25)))
+    _eig_ok((W * np.logspace(-10, 3, 25)) @ W.conj().T)
+    T = np.diag(np.arange(10.0)) + np.diag(np.full(9, 1e-300), 1) + np.diag(np.full(9, 1e-300), -1)
+    _eig_ok(T.astype(complex))
+    _eig_ok(np.array([[1.0, 2 - 1j], [2 + 1j, -3.0]]))
+    w, Z = ovl.hermitian_eig(np.zeros((5, 5), complex))
+    assert np.all(w == 0) and np.allclose(Z.conj().T @ Z, np.eye(5))
 
 
 def test_host_hermitian_eig_degenerate_and_diagonal():
