@@ -339,6 +339,11 @@ typedef struct {
 /* slots: concurrent requests (1..64); hbm_budget: bytes of device memory the server may use
  * (0 = 90% of the free memory at creation). */
 ovl_status ovl_server_create(ovl_server **srv, int slots, size_t hbm_budget);
+/* Host only (no device call): the device memory the server reserves for req at admission,
+ * an upper estimate of what ovl_create and ovl_solve allocate for its lattice, precision,
+ * preconditioner, sign method, deflation and right-hand sides (params NULL = defaults).
+ * OVL_EINVAL for NULL pointers, n_rhs < 1 or a non-positive extent. */
+ovl_status ovl_request_bytes(const ovl_request *req, size_t *bytes);
 /* Queues a request and returns its ticket. The buffers it points to (gauge, b, x) must stay
  * valid until the request is done. OVL_ENOMEM: the request can never fit the budget. */
 ovl_status ovl_server_submit(ovl_server *srv, const ovl_request *req, long *ticket);

@@ -98,7 +98,7 @@ class ovl_prof(ctypes.Structure):
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
-           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
+           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "ovl_request_bytes", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
            "ovl_apply_n", "ovl_dslash_time_n", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
@@ -132,6 +132,7 @@ def lib():
         L.ovl_hermitian_eig.argtypes = [I_, P, P, P]
         L.ovl_deflation_info.argtypes = [P, ctypes.POINTER(I_), P, ctypes.POINTER(D), ctypes.POINTER(D),
                                          ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
+        L.ovl_request_bytes.argtypes = [ctypes.POINTER(ovl_request), ctypes.POINTER(ctypes.c_size_t)]
         L.ovl_krylov_sign_info.argtypes = [P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]
         L.wilson_apply_noalloc.argtypes = [P, P, P, P, D, I_, P]
         L.ovl_dslash_time.argtypes = [P, I_, I_, ctypes.POINTER(D)]
@@ -283,6 +284,18 @@ def ovl_deflation_info(ctx):
                                     ctypes.byref(res), ctypes.byref(mv)), ctx)
     return {"k": k.value, "lambda": lam[:k.value].tolist(), "lambda_next": nxt.value, "setup_s": t.value,
             "resid_max": res.value, "matvecs": mv.value}
+
+
+def request_bytes(dims, n_rhs=1, params=None):
+    """Device bytes the serving loop reserves for a request (host-side estimate, no GPU)."""
+    req = ovl_request()
+    for m in range(4):
+        req.dims[m] = int(dims[m])
+    req.n_rhs = int(n_rhs)
+    req.params = ctypes.cast(ctypes.byref(params), ctypes.c_void_p).value if params is not None else None
+    out = ctypes.c_size_t()
+    _check(lib().ovl_request_bytes(ctypes.byref(req), ctypes.byref(out)))
+    return out.value
 
 
 def ovl_krylov_sign_info(ctx):

@@ -98,6 +98,14 @@ size_t estimate_bytes(const ovl_request &r, const ovl_params &p) {
     b += (p.n_poles + 3) * v64;                           // FP64 multishift
     const bool mixed = p.precision != OVL_FP64 || p.precond == OVL_PREC_RECURSIVE;
     if (mixed) b += (p.n_poles + 3) * v32;                 // FP32 multishift
+    if (p.sign_method == OVL_SIGN_KRYLOV) b += (p.krylov_m + p.krylov_keep + 3) * v64;   // Krylov sign basis
+    if (p.n_deflate > 0) {
+        // eigenvectors xi, gamma5 xi (FP64 and FP32) and scratch, plus the eigensolver's basis
+        // while the context is created (basis m + 1, kept Ritz vectors, one scratch vector)
+        const int k = p.n_deflate, mmax = std::min(2 * (k + 1) + 32, 120);
+        const int nkeep = std::min(k + 17, mmax - 16);
+        b += (2 * k + 1) * v64 + (2 * k + 1) * v32 + (mmax + nkeep + 2) * v64;
+    }
     const int nrhs = r.n_rhs;
     if (nrhs > 1 && p.rhs_block > 1) {
         const int nb = std::min(std::min(p.rhs_block, nrhs), 12);
@@ -248,6 +256,17 @@ extern "C" ovl_status ovl_server_create(ovl_server **srv, int slots, size_t hbm_
     s->budget = hbm_budget ? std::min(hbm_budget, fr) : (size_t)(0.9 * (double)fr);
     for (int k = 0; k < slots; k++) s->workers.emplace_back(worker, s);
     *srv = s;
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_request_bytes(const ovl_request *req, size_t *bytes) {
+    if (!req || !bytes || req->n_rhs < 1) return OVL_EINVAL;
+    for (int m = 0; m < 4; m++)
+        if (req->dims[m] < 1) return OVL_EINVAL;
+    ovl_params p;
+    if (req->params) p = *req->params;
+    else ovl_params_default(&p);
+    *bytes = estimate_bytes(*req, p);
     return OVL_OK;
 }
 

@@ -130,3 +130,21 @@ def test_host_hermitian_eig_degenerate_and_diagonal():
     assert np.allclose(w, [-2.0, 1.0, 1.0, 3.0])
     with pytest.raises(ovl.OvlError):
         ovl.hermitian_eig(np.zeros((0, 0), dtype=complex))
+
+
+def test_request_bytes_estimate_covers_options():
+    """The serving loop's admission estimate (host only) grows by the Krylov sign basis and
+    the deflation vectors when those options are on, scales with the volume, and rejects
+    bad requests."""
+    dims = (16, 16, 16, 16)
+    v64 = 24 * 16 ** 4 * 8
+    base = ovl.request_bytes(dims)
+    kry = ovl.request_bytes(dims, params=ovl.params_default(sign_method=ovl.OVL_SIGN_KRYLOV, krylov_m=40,
+                                                            krylov_keep=8))
+    assert kry - base >= (40 + 8 + 3) * v64
+    defl = ovl.request_bytes(dims, params=ovl.params_default(n_deflate=16))
+    assert defl - base >= (2 * 16 + 1) * v64 + (66 + 33 + 2) * v64
+    assert ovl.request_bytes((32, 32, 32, 32)) > 15 * base
+    assert ovl.request_bytes(dims, n_rhs=4) > base
+    with pytest.raises(ovl.OvlError):
+        ovl.request_bytes((0, 4, 4, 4))
