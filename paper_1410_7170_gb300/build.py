@@ -32,11 +32,21 @@ def _sources():
     return cu, cxx
 
 
-def _stale(obj, deps):
+def _stale(obj, deps, cmd=None):
+    """True if obj is missing, older than a dependency, or was compiled with another command
+    (the command of the last successful compile is kept beside the object)."""
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    return any(os.path.getmtime(d) > t for d in deps)
+    if any(os.path.getmtime(d) > t for d in deps):
+        return True
+    if cmd is not None:
+        try:
+            with open(obj + ".cmd") as f:
+                return f.read() != " ".join(cmd)
+        except OSError:
+            return True
+    return False
 
 
 def build(force=False, verbose=False):
@@ -58,18 +68,20 @@ def build(force=False, verbose=False):
         obj = os.path.join(OUT_DIR, s + ".o")
         cmd = ["g++", "-O2", "-fcx-limited-range", "-std=c++17", "-fPIC", "-c", src, "-o", obj]
         jobs.append((obj, src, cmd))
-    todo = [(o, c) for o, s, c in jobs if force or _stale(o, [s] + headers)]
+    todo = [(o, c) for o, s, c in jobs if force or _stale(o, [s] + headers, c)]
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, r
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        for cmd, r in ex.map(lambda oc: run(oc[1]), todo):
+        for (obj, _), (cmd, r) in zip(todo, ex.map(lambda oc: run(oc[1]), todo)):
             if r.returncode != 0:
                 raise RuntimeError("compile failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
             if verbose and (r.stdout or r.stderr):
                 sys.stderr.write(r.stdout + r.stderr)
+            with open(obj + ".cmd", "w") as f:
+                f.write(" ".join(cmd))
     objs = [o for o, _, _ in jobs]
     if force or todo or _stale(LIB, objs):
         cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs]

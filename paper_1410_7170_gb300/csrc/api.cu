@@ -1,9 +1,11 @@
 // C-ABI entry points and the host-side control of the solvers.
 //
 //   ovl_create   gauge upload/compression, spectral bounds of |Q| by Lanczos on Q^2,
-//                Zolotarev coefficients, sigma_min by power iteration (Sec. 5.1)
+//                Zolotarev coefficients, optional low-mode deflation, sigma_min of
+//                Eq. (default_m) by Lanczos on Q(0)^2 (Sec. 5.1)
 //   wilson_apply D_W(m0) (Eq. Wilson-Dirac)
-//   sign_apply   sign(Q) by Zolotarev + multishift CG
+//   sign_apply   sign(Q) by Zolotarev + multishift CG, or by the restarted Krylov method
+//                of Sec. 5.2 (krylov.cu)
 //   ovl_apply    D_N = rho I + Gamma5 sign(Q) (Eq. overlap_def)
 //   ovl_solve    GMRES(m) / FGMRES(m) on D_N psi = eta (Eq. linsys, Sec. 5.1-5.3)
 #include <math.h>
@@ -11,10 +13,14 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <complex>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ovl.h"
@@ -737,8 +743,6 @@ ovl_status Ctx::lanczos_bounds(double *lmin, double *lmax, double m0) {
     return OVL_OK;
 }
 
-// sigma~_max of D_W(0) by power iteration; sigma~_min = 8 - sigma~_max rounded up to
-// one decimal (Sec. 5.1).
 // sigma_min of Eq. (default_m): the smallest real part of the eigenvalues of D_W(0). It is
 // estimated by the smallest singular value of D_W(0), i.e. the smallest |eigenvalue| of the
 // Hermitian Q(0) = Gamma5 D_W(0), from the Lanczos run on Q(0)^2 (its extreme eigenvalues
@@ -757,10 +761,6 @@ ovl_status Ctx::sigma_min_estimate(double *smin) {
 // Threads per site of the stencils (1 or 4) for this lattice shape: both variants of
 // each precision are timed with CUDA events on the context's stream and the faster is
 // kept. Results are cached per process and shape.
-#include <map>
-#include <mutex>
-#include <tuple>
-#include <array>
 static std::mutex g_tune_mu;
 struct TuneEntry {
     int tps64, tps32;
