@@ -351,7 +351,7 @@ def sign_methods(ovl, torch, U, b, dev, stream, info, tol=1e-10, reps=3):
             with torch.cuda.stream(stream):
                 op.sign_apply(out, b_d, tol)
             torch.cuda.synchronize()
-            products = op.prof_get(reset=True)["ms_stencil_f64"]["launches"]   # one Q^2 per iteration
+            products = op.prof_get(reset=True)["ms_shifts_f64"]["launches"]   # one launch (one Q^2) per iteration
             op.prof_enable(False)
         else:
             products = (k1["matvecs"] - k0["matvecs"]) / reps

@@ -235,11 +235,22 @@ void Ctx::fill_poles(MsState &s, int n, double tol) const {
     s.beta_prev = 0.0;
     const std::vector<double> &a = zs_a[n - 1], &c = zs_c[n - 1];
     const double d0 = zs_d0[n - 1];
+    // The residual r_l of shift l adds (d0/lmin) a_l lmin^2 Q (Q^2 + sigma_l)^{-1} r_l to sign(Q) b.
+    // With |Q| in [lmin, lmax] (the interval the rational approximation assumes) its norm is at
+    // most d0 |a_l| g_l ||r_l||, g_l = max of x/(x^2 + c_l) over x in [1, lmax/lmin]. Shift l is
+    // dropped once that bound is below its share of tol ||b||: half for the smallest shift (the
+    // slowest to converge), the other half split evenly; the shares sum to 1.
+    const double K = lam_max / lam_min;
+    int l_small = 0;
+    for (int l = 1; l < n; l++)
+        if (c[l] < c[l_small]) l_small = l;
     for (int l = 0; l < n; l++) {
         s.sigma[l] = lam_min * lam_min * c[l];
         s.w[l] = a[l] * lam_min * lam_min;
-        // ||(d0/lmin) Q w_l (Q^2+sigma_l)^{-1} r_l|| <= d0 |a_l| ||r_l|| / (2 sqrt(c_l)); summed over l
-        s.crit[l] = n * d0 * fabs(a[l]) / (2.0 * sqrt(c[l]));
+        const double rc = sqrt(c[l]);
+        const double g = rc <= 1.0 ? 1.0 / (1.0 + c[l]) : (rc >= K ? K / (K * K + c[l]) : 0.5 / rc);
+        const double share = n == 1 ? 1.0 : (l == l_small ? 0.5 : 0.5 / (n - 1));
+        s.crit[l] = d0 * fabs(a[l]) * g / share;
         s.zeta[l] = 1.0;
         s.zeta_prev[l] = 1.0;
         s.active[l] = 1;
