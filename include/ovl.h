@@ -8,7 +8,8 @@
  * kernel mass m0_ker = -rho_in and rho = (-mu/2 + m0_ker)/(mu/2 + m0_ker) (Sec. 5).
  * sign(Q), Q = Gamma5 D_W, is evaluated with Zolotarev's optimal rational
  * approximation on [lambda_min, lambda_max] of |Q| and a multishift conjugate
- * gradient for the shifted systems (Q^2 + sigma_l) x_l = b. D_N psi = eta
+ * gradient for the shifted systems (Q^2 + sigma_l) x_l = b, or (params.sign_method)
+ * by the restarted Krylov method with thick restarts of Sec. 5.2. D_N psi = eta
  * (Eq. linsys) is solved by restarted GMRES(m) or right-preconditioned
  * FGMRES(m) in FP64 (Sec. 5.1), optionally with relaxation of the sign
  * accuracy (Sec. 5.2) and a Wilson-Dirac preconditioner D_W(m0_prec)^{-1}
@@ -212,11 +213,14 @@ ovl_status wilson_apply_n(ovl_ctx *ctx, double *out, const double *in, int n_rhs
 
 /* out_k ~= D_N in_k for k < n_rhs (Eq. overlap_def), all right-hand sides of a block of up
  * to 12 evaluated by one lock-step FP64 multishift CG on the multi-RHS stencil; sign accuracy
- * tol for each. */
+ * tol for each. With deflation or the Krylov sign the right-hand sides run one at a time. */
 ovl_status ovl_apply_n(ovl_ctx *ctx, double *out, const double *in, int n_rhs, double tol);
 
-/* out ~= sign(Q) in, Q = Gamma5 D_W(m0_ker), to relative accuracy tol (>= 1e-14):
- * Zolotarev rational approximation + FP64 multishift CG (Sec. 2, Eq. overlap_def). */
+/* out ~= sign(Q) in, Q = Gamma5 D_W(m0_ker), to relative accuracy tol (>= 1e-14), in FP64:
+ * Zolotarev rational approximation + multishift CG (Sec. 2, Eq. overlap_def), or the
+ * restarted Krylov method of Sec. 5.2 when params.sign_method = OVL_SIGN_KRYLOV. The
+ * multishift stops when its error bound over [lambda_min, lambda_max] is below tol ||in||
+ * (with the Zolotarev degree chosen so that its uniform error is <= tol / 10). */
 ovl_status sign_apply(ovl_ctx *ctx, double *out, const double *in, double tol);
 
 /* out ~= D_N in = rho in + Gamma5 sign(Q) in (Eq. overlap_def), sign to accuracy tol. */
