@@ -20,10 +20,13 @@ paper defines:
                    FGMRES(m) (Sec. 5.1)
   * krylov_sign.py the restarted Krylov sign function of Sec. 5.2
                    (quadrature-based restarts, optional thick restarts)
+  * sap.py         red-black multiplicative Schwarz with minimal-residual
+                   block solves (the Wilson preconditioner's smoother, Sec. 5.1)
 
 Every function is pinned by tests against closed forms, invariants or
 library routines (free-field spectrum, Gamma5-hermiticity, sign^2 = I,
 Ginsparg-Wilson, normality, gauge covariance, Prop. Fnorm, the alternation
 theorem for the Zolotarev coefficients, an SVD polar factor for sign(Q), the
-closed form of restarted Arnoldi for matrix functions).
+closed form of restarted Arnoldi for matrix functions, block Gauss-Seidel
+for one Schwarz cycle with exact block solves).
 """
