@@ -175,6 +175,18 @@ ovl_status wilson_apply(ovl_ctx *ctx, double *out, const double *in, double m0);
  * (nullable) receives the FGMRES iteration count. Needs even sap_block extents dividing dims. */
 ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, double m0, double tol, int *iters);
 
+/* out = M_SAP in, one application of the Schwarz preconditioner that wilson_solve (and the
+ * overlap solver's Wilson preconditioner) uses, on D_W(m0): params.sap_cycles red-black
+ * multiplicative Schwarz cycles from out = 0 over blocks of params.sap_block sites, coloured
+ * by the parity of their block coordinates (colour 0 first); per colour the residual
+ * in - D_W out is formed once and every block of that colour adds params.sap_mr_iters
+ * minimal-residual steps on its block-local D_W (hops leaving the block dropped). The
+ * paper's smoother is a red-black multiplicative Schwarz method (Sec. 5.1) whose block
+ * solver it does not specify. FP32 unless params.precision == OVL_FP64. OVL_EINVAL for
+ * sap_block extents that are odd, do not divide dims or exceed 256 sites, and for
+ * sap_cycles or sap_mr_iters < 1. */
+ovl_status wilson_sap_apply(ovl_ctx *ctx, double *out, const double *in, double m0);
+
 /* Stencil variant chosen by the autotuner (threads per site, 1 or 4, for FP64 and FP32)
  * and the measured ms per full-lattice stencil application of each variant
  * (ms[0..3] = FP64 x1, FP64 x4, FP32 x1, FP32 x4; zeros when forced). Nullable outputs. */

@@ -98,7 +98,7 @@ class ovl_prof(ctypes.Structure):
 
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
-           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "ovl_request_bytes", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
+           "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "ovl_request_bytes", "wilson_sap_apply", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
            "ovl_apply_n", "ovl_dslash_time_n", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
@@ -127,6 +127,7 @@ def lib():
         L.ovl_prof_enable.argtypes = [P, I_]
         L.ovl_prof_get.argtypes = [P, ctypes.POINTER(ovl_prof), I_]
         L.wilson_solve.argtypes = [P, P, P, D, D, ctypes.POINTER(I_)]
+        L.wilson_sap_apply.argtypes = [P, P, P, D]
         L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
         L.ovl_tuning_sap.argtypes = [P, ctypes.POINTER(I_), P]
         L.ovl_hermitian_eig.argtypes = [I_, P, P, P]
@@ -245,6 +246,12 @@ def wilson_apply_noalloc(out, inp, gauge, dims, m0, antiperiodic=True, stream=No
     _check(lib().wilson_apply_noalloc(_ptr(out, True), _ptr(inp), _ptr(gauge), ctypes.cast(d, ctypes.c_void_p),
                                       float(m0), int(bool(antiperiodic)),
                                       ctypes.c_void_p(stream) if stream else None), None)
+    return out
+
+
+def wilson_sap_apply(ctx, out, inp, m0):
+    """out = M_SAP inp: one application of the Schwarz preconditioner on D_W(m0)."""
+    _check(lib().wilson_sap_apply(ctx, _ptr(out, True), _ptr(inp), float(m0)), ctx)
     return out
 
 
@@ -388,6 +395,9 @@ class Overlap:
 
     def wilson_solve(self, x, b, m0, tol):
         return wilson_solve(self.ctx, x, b, m0, tol)
+
+    def sap_apply(self, out, inp, m0):
+        return wilson_sap_apply(self.ctx, out, inp, m0)
 
     def tuning(self):
         return ovl_tuning(self.ctx)

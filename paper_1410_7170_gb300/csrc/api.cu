@@ -1284,6 +1284,33 @@ extern "C" ovl_status wilson_solve(ovl_ctx *ctx, double *x, const double *b, dou
     return c->export_vec(c->io_b, x);
 }
 
+extern "C" ovl_status wilson_sap_apply(ovl_ctx *ctx, double *out, const double *in, double m0) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    if (!isfinite(m0)) {
+        c->err = "m0 must be finite";
+        return OVL_EINVAL;
+    }
+    for (int m = 0; m < 4; m++) {
+        if (c->p.sap_block[m] < 2 || (c->p.sap_block[m] & 1) || c->g.L[m] % c->p.sap_block[m] ||
+            c->p.sap_block[0] * c->p.sap_block[1] * c->p.sap_block[2] * c->p.sap_block[3] > 256) {
+            c->err = "sap_block must be even, divide the lattice extent and hold <= 256 sites";
+            return OVL_EINVAL;
+        }
+    }
+    if (c->p.sap_cycles < 1 || c->p.sap_mr_iters < 1) {
+        c->err = "sap_cycles and sap_mr_iters must be >= 1";
+        return OVL_EINVAL;
+    }
+    if (!c->sap_tuned) {
+        ST(c->autotune_sap());
+        c->sap_tuned = true;
+    }
+    ST(c->import_vec(in, c->io_a));
+    ST(sap_apply_eo(c, c->io_a, c->io_b, m0));
+    return c->export_vec(c->io_b, out);
+}
+
 extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !ms || reps < 1 || (precision != 0 && precision != 1)) return OVL_EINVAL;

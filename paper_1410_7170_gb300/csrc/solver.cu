@@ -365,6 +365,34 @@ ovl_status wilson_solve_eo(Ctx *c, const double2 *b, double2 *x, double m0, doub
     return OVL_OK;
 }
 
+// One application of the Schwarz preconditioner, x = M_SAP b: params.sap_cycles red-black
+// cycles from x = 0 over params.sap_block blocks, params.sap_mr_iters MR steps per block
+// solve, on D_W(m0); FP64 even-odd spinors in and out, FP32 inside unless precision ==
+// OVL_FP64. The same call the Wilson FGMRES makes for its preconditioner.
+ovl_status sap_apply_eo(Ctx *c, const double2 *b, double2 *x, double m0) {
+    SapGeom sg = make_sap_geom(c->g, c->p.sap_block);
+    sg.tps = c->sap_tps;
+    if (c->p.precision == OVL_FP64) {
+        if (!c->sap_r64) {
+            void *buf;
+            ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double)));
+            c->sap_r64 = buf;
+        }
+        CK(Ops<double>::sap(c, sg, (const double *)b, (double *)x, (double *)c->sap_r64, m0));
+        return OVL_OK;
+    }
+    ST(ensure_f32_buffers(c));
+    if (!c->sap_r32) {
+        void *buf;
+        ST(c->alloc(&buf, (size_t)c->n64 * sizeof(float)));
+        c->sap_r32 = buf;
+    }
+    CK(spinor_d2f(c->g, b, (float4 *)c->f_a, c->stream));
+    CK(Ops<float>::sap(c, sg, c->f_a, c->f_b, (float *)c->sap_r32, m0));
+    CK(spinor_f2d(c->g, (const float4 *)c->f_b, x, c->stream));
+    return OVL_OK;
+}
+
 int batch_size_for(Ctx *c, int want);
 // Most accurate sign request the lower-precision multishift serves in the mixed modes:
 // FP32 vectors (the accuracy floor of the inner requests too), FP16-stored directions (11

@@ -218,5 +218,7 @@ ovl_status solve_batch(Ctx *c, double2 *x, const double2 *b, int nrhs, double to
                        double *worst_res, bool *all_conv);
 // Inexact Wilson solve on FP64 even-odd spinors (FP32 inside unless precision == FP64).
 ovl_status wilson_solve_eo(Ctx *c, const double2 *b, double2 *x, double m0, double tol, int *iters);
+// One Schwarz preconditioner application x = M_SAP b on FP64 even-odd spinors.
+ovl_status sap_apply_eo(Ctx *c, const double2 *b, double2 *x, double m0);
 
 }  // namespace ovl
