@@ -1,7 +1,7 @@
 """Runs one operation of a workload through the library's public API, for external
 profilers (ncu). Nothing is timed here; the benchmark is bench.py.
 
-    python -m paper_1410_7170_gb300.profile_run --what solve_mixed|solve_fp64|sign64|dslash64|dslash32
+    python -m paper_1410_7170_gb300.profile_run --what solve_mixed|solve_fp64|sign64|sign64_krylov|sap|dslash64|dslash32
         [--lattice 16x16x16x16] [--stout 3] [--stencil-tps 1] [--sap-tps 1]
 
 The gauge field, right-hand side and solver settings are those of bench.py's 16^4
@@ -27,7 +27,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--what", required=True,
-                    choices=["solve_mixed", "solve_fp64", "sign64", "dslash64", "dslash32"])
+                    choices=["solve_mixed", "solve_fp64", "sign64", "sign64_krylov", "sap", "dslash64", "dslash32"])
     ap.add_argument("--lattice", default="16x16x16x16")
     ap.add_argument("--stout", type=int, default=3)
     ap.add_argument("--stencil-tps", type=int, default=0)
@@ -42,6 +42,10 @@ def main():
         p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, **tune)
     elif a.what == "solve_fp64":
         p = ovl.params_default(precond=ovl.OVL_PREC_WILSON, precision=ovl.OVL_FP64, prec_max_iter=4, **tune)
+    elif a.what == "sign64_krylov":
+        p = ovl.params_default(sign_method=ovl.OVL_SIGN_KRYLOV, **tune)
+    elif a.what == "sap":
+        p = ovl.params_default(precision=ovl.OVL_MIXED_FP32, **tune)
     else:
         p = ovl.params_default(**tune)
     op = ovl.Overlap(U, dims, 1.0, 0.01, p)
@@ -49,8 +53,10 @@ def main():
     if a.what.startswith("solve"):
         st, stats = op.ovl_solve(x, b, 1, 1e-8)
         print(stats)
-    elif a.what == "sign64":
+    elif a.what in ("sign64", "sign64_krylov"):
         op.sign_apply(x, b, 1e-8)
+    elif a.what == "sap":
+        op.sap_apply(x, b, -0.266)   # m0^def of the 16^4 workload field (Eq. default_m)
     else:
         print(op.dslash_time(0 if a.what == "dslash64" else 1, 3), "ms")
     torch.cuda.synchronize()
