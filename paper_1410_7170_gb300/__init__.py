@@ -25,12 +25,15 @@ _STATUS = {0: "OVL_OK", 1: "OVL_EINVAL", 2: "OVL_ENOMEM", 3: "OVL_ENOCONV", 4: "
 
 
 class OvlError(RuntimeError):
+    """A non-OK ovl_status, with the library's one-line reason."""
+
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
         self.status = status
 
 
 class ovl_params(ctypes.Structure):
+    """Mirror of ovl_params in include/ovl.h (same fields, same order)."""
     _fields_ = [
         ("tol_outer", ctypes.c_double), ("restart", ctypes.c_int), ("relax", ctypes.c_int),
         ("relax_factor", ctypes.c_double), ("n_poles", ctypes.c_int), ("lambda_min", ctypes.c_double),
@@ -48,6 +51,7 @@ class ovl_params(ctypes.Structure):
 
 
 class ovl_stats(ctypes.Structure):
+    """Mirror of ovl_stats (per-solve statistics)."""
     _fields_ = [
         ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("ms_iters_fp64", ctypes.c_long),
         ("ms_iters_low", ctypes.c_long), ("prec_iters", ctypes.c_long), ("true_rel_resid", ctypes.c_double),
@@ -60,6 +64,7 @@ class ovl_stats(ctypes.Structure):
 
 
 class ovl_request(ctypes.Structure):
+    """Mirror of ovl_request (one serving request)."""
     _fields_ = [("gauge", ctypes.c_void_p), ("gauge_key", ctypes.c_long), ("dims", ctypes.c_int * 4),
                 ("rho", ctypes.c_double), ("mu", ctypes.c_double), ("n_rhs", ctypes.c_int),
                 ("b", ctypes.c_void_p), ("x", ctypes.c_void_p), ("tol", ctypes.c_double),
@@ -67,6 +72,7 @@ class ovl_request(ctypes.Structure):
 
 
 class ovl_result(ctypes.Structure):
+    """Mirror of ovl_result (a served request's outcome)."""
     _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("stats", ovl_stats),
                 ("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("message", ctypes.c_char * 160)]
@@ -78,6 +84,7 @@ class ovl_result(ctypes.Structure):
 
 
 class ovl_prof_kernel(ctypes.Structure):
+    """Mirror of ovl_prof_kernel (counters of one kernel class)."""
     _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_long), ("bytes", ctypes.c_double),
                 ("flops", ctypes.c_double), ("timed", ctypes.c_long), ("timed_bytes", ctypes.c_double)]
 
@@ -86,6 +93,7 @@ PROF_KERNELS = ["ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_
 
 
 class ovl_prof(ctypes.Structure):
+    """Mirror of ovl_prof (instrumentation counters)."""
     _fields_ = [("launches", ctypes.c_long), ("k", ovl_prof_kernel * 4), ("valid", ctypes.c_int)]
 
     def as_dict(self):
@@ -176,6 +184,8 @@ def _check(st, ctx=None):
 
 
 def params_default(**kw):
+    """ovl_params with the library's defaults (Table 2 / Table 3 values where the paper gives
+    one), then the given fields set by name (sap_block as a 4-sequence)."""
     p = ovl_params()
     _check(lib().ovl_params_default(ctypes.byref(p)))
     for k, v in kw.items():
@@ -199,7 +209,8 @@ def ovl_zolotarev(k, n):
 
 
 def ovl_create(gauge, dims, rho, mu, params=None, stream=None):
-    import numpy as np
+    """New context for D_N with kernel mass -rho and overlap mass mu on the lattice dims;
+    gauge: [V][4][3][3] complex128 (host or device); stream: a cudaStream_t handle or None."""
     ctx = ctypes.c_void_p()
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
     st = lib().ovl_create(ctypes.byref(ctx), _ptr(gauge), ctypes.cast(d, ctypes.c_void_p), float(rho),
@@ -210,21 +221,25 @@ def ovl_create(gauge, dims, rho, mu, params=None, stream=None):
 
 
 def ovl_destroy(ctx):
+    """Frees the context and its device memory (None is a no-op)."""
     if ctx:
         _check(lib().ovl_destroy(ctx))
 
 
 def wilson_apply(ctx, out, inp, m0):
+    """out = D_W(m0) inp (Eq. Wilson-Dirac); [V][4][3] complex128 buffers, host or device."""
     _check(lib().wilson_apply(ctx, _ptr(out, True), _ptr(inp), float(m0)), ctx)
     return out
 
 
 def sign_apply(ctx, out, inp, tol):
+    """out ~= sign(Gamma5 D_W(m0_ker)) inp to relative accuracy tol (FP64)."""
     _check(lib().sign_apply(ctx, _ptr(out, True), _ptr(inp), float(tol)), ctx)
     return out
 
 
 def ovl_apply(ctx, out, inp, tol):
+    """out ~= D_N inp = rho inp + Gamma5 sign(Q) inp (Eq. overlap_def), sign to accuracy tol."""
     _check(lib().ovl_apply(ctx, _ptr(out, True), _ptr(inp), float(tol)), ctx)
     return out
 
@@ -263,6 +278,7 @@ def wilson_solve(ctx, x, b, m0, tol):
 
 
 def ovl_tuning(ctx):
+    """Stencil threads per site chosen by the autotuner (FP64, FP32) and the timed variants (ms)."""
     import numpy as np
     a, b = ctypes.c_int(), ctypes.c_int()
     ms = np.zeros(4, dtype=np.float32)
@@ -282,6 +298,8 @@ def hermitian_eig(A):
 
 
 def ovl_deflation_info(ctx):
+    """Deflated eigenvalues of Q, |lambda_{k+1}|, setup seconds, worst eigenpair residual and the
+    eigensolver's Q^2 products (k = 0 without deflation)."""
     import numpy as np
     k = ctypes.c_int()
     _check(lib().ovl_deflation_info(ctx, ctypes.byref(k), None, None, None, None, None), ctx)
@@ -306,12 +324,14 @@ def request_bytes(dims, n_rhs=1, params=None):
 
 
 def ovl_krylov_sign_info(ctx):
+    """Cycles and Q^2 products of the restarted Krylov sign function since the context was made."""
     cyc, mv = ctypes.c_long(), ctypes.c_long()
     _check(lib().ovl_krylov_sign_info(ctx, ctypes.byref(cyc), ctypes.byref(mv)), ctx)
     return {"cycles": cyc.value, "matvecs": mv.value}
 
 
 def ovl_tuning_sap(ctx):
+    """Threads per block site of the FP32 Schwarz block solves and the timed variants (ms)."""
     import numpy as np
     a = ctypes.c_int()
     ms = np.zeros(3, dtype=np.float32)
@@ -327,22 +347,26 @@ def ovl_dslash_time(ctx, precision, reps=20):
 
 
 def wilson_apply_n(ctx, out, inp, n_rhs, m0):
+    """out_k = D_W(m0) inp_k for n_rhs vectors back to back (multi-RHS stencil)."""
     _check(lib().wilson_apply_n(ctx, _ptr(out, True), _ptr(inp), int(n_rhs), float(m0)), ctx)
     return out
 
 
 def ovl_apply_n(ctx, out, inp, n_rhs, tol):
+    """out_k ~= D_N inp_k for n_rhs vectors back to back (lock-step batched multishift)."""
     _check(lib().ovl_apply_n(ctx, _ptr(out, True), _ptr(inp), int(n_rhs), float(tol)), ctx)
     return out
 
 
 def ovl_dslash_time_n(ctx, precision, nrhs, reps=20):
+    """ms per launch of the multi-RHS stencil on nrhs right-hand sides (0 = FP64, 1 = FP32)."""
     ms = ctypes.c_double()
     _check(lib().ovl_dslash_time_n(ctx, int(precision), int(nrhs), int(reps), ctypes.byref(ms)), ctx)
     return ms.value
 
 
 def ovl_info(ctx):
+    """Spectral interval of |Q|, Zolotarev error bound, rho, m0_ker, m0_prec and sigma_min."""
     vals = [ctypes.c_double() for _ in range(7)]
     _check(lib().ovl_info(ctx, *[ctypes.byref(v) for v in vals]), ctx)
     keys = ["lambda_min", "lambda_max", "delta", "rho", "m0_ker", "m0_prec", "sigma_min"]
@@ -350,10 +374,12 @@ def ovl_info(ctx):
 
 
 def ovl_prof_enable(ctx, on=True):
+    """Switches the multishift event instrumentation on or off."""
     _check(lib().ovl_prof_enable(ctx, int(bool(on))), ctx)
 
 
 def ovl_prof_get(ctx, reset=False):
+    """Instrumentation counters per kernel class (launches, timed ms, algorithmic bytes/flops)."""
     out = ovl_prof()
     _check(lib().ovl_prof_get(ctx, ctypes.byref(out), int(bool(reset))), ctx)
     return out.as_dict()
