@@ -53,7 +53,7 @@ typedef enum {
     OVL_ENOMEM = 2,       /* device memory / HBM budget exhausted */
     OVL_ENOCONV = 3,      /* iteration cap reached before the tolerance */
     OVL_EBREAKDOWN = 4,   /* Krylov breakdown (zero or non-finite scalar) */
-    OVL_ETIMEOUT = 5,     /* device-side iteration watchdog gave up */
+    OVL_ETIMEOUT = 5,     /* ovl_solve passed its wall-clock limit (params.max_seconds) */
     OVL_ECUDA = 6         /* CUDA runtime error */
 } ovl_status;
 
@@ -63,6 +63,18 @@ typedef enum {
     OVL_MIXED_HALF = 2,   /* as MIXED_FP32, inner multishift vectors stored in FP16 */
     OVL_MIXED_BF16 = 3    /* as MIXED_FP32, inner multishift vectors stored in BF16 */
 } ovl_precision;
+
+/* Arithmetic of one operator application through the *_arith entry points (the solver's
+ * own choice follows ovl_params.precision and ff_outer). */
+typedef enum {
+    OVL_ARITH_FP64 = 0,   /* FP64 storage and arithmetic */
+    OVL_ARITH_FF = 1,     /* float-float: each real is an unevaluated sum of two FP32 numbers (about
+                             48 significant bits), computed on the FP32 pipes; same bytes as FP64 */
+    OVL_ARITH_FP32 = 2,   /* FP32 storage and arithmetic (links stored as 12 reals) */
+    OVL_ARITH_FP16 = 3,   /* sign only: FP32 arithmetic, the multishift's shifted directions stored
+                             in FP16 with a per-site FP32 scale */
+    OVL_ARITH_BF16 = 4    /* sign only: FP32 arithmetic, shifted directions stored in BF16 */
+} ovl_arith;
 
 typedef enum {
     OVL_PREC_NONE = 0,      /* GMRES(m), no preconditioner (Sec. 5.1 baseline) */
@@ -127,6 +139,14 @@ typedef struct {
     int krylov_m;           /* basis vectors per cycle of the Krylov sign (4..120; default 40) */
     int krylov_keep;        /* Ritz vectors of the smallest Ritz values of Q^2 kept at a restart
                                (thick restart; 0 = plain restart; <= krylov_m - 2; default 8) */
+    int ff_outer;           /* 1 (default): in the mixed precisions (precision != OVL_FP64) the outer
+                               solver's sign applications that need more than FP32 accuracy run in
+                               float-float arithmetic (OVL_ARITH_FF) instead of native FP64; the
+                               outer residuals, Arnoldi vectors and reductions stay FP64. 0: native
+                               FP64 for them. Ignored with precision == OVL_FP64 */
+    double max_seconds;     /* wall-clock limit of one ovl_solve call (0 = none, the default): checked on
+                               the host after every chunk of multishift iterations; past it the call
+                               returns OVL_ETIMEOUT (x unspecified) and the context stays usable */
 } ovl_params;
 
 /* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
@@ -144,7 +164,9 @@ typedef struct {
     double t_prec;          /* wall time inside inexact Wilson solves (single-RHS path); the rest
                                of `seconds` is (F)GMRES orthogonalisation and host work. The phase
                                times are exact (stream synchronised at each phase end) only while
-                               ovl_prof_enable is on. */
+                               ovl_prof_enable is on. t_sign_fp64 includes the float-float sign. */
+    long ms_iters_ff;       /* multishift CG iterations of FP64-accuracy sign applications run in
+                               float-float arithmetic (params.ff_outer) */
 } ovl_stats;
 
 /* Fills *p with the defaults. Returns OVL_EINVAL if p is NULL. */
@@ -232,7 +254,11 @@ ovl_status ovl_apply_n(ovl_ctx *ctx, double *out, const double *in, int n_rhs, d
  * Zolotarev rational approximation + multishift CG (Sec. 2, Eq. overlap_def), or the
  * restarted Krylov method of Sec. 5.2 when params.sign_method = OVL_SIGN_KRYLOV. The
  * multishift stops when its error bound over [lambda_min, lambda_max] is below tol ||in||
- * (with the Zolotarev degree chosen so that its uniform error is <= tol / 10). */
+ * (with the Zolotarev degree chosen so that its uniform error is <= tol / 10).
+ * OVL_ENOCONV if the multishift reached params.max_ms_iter: out then holds the result formed
+ * from the last iterate. OVL_EBREAKDOWN if a CG scalar became zero or non-finite (for
+ * instance ||in||^2 overflowing FP64); out is then unspecified. (sign_apply_arith and
+ * ovl_apply behave the same way.) */
 ovl_status sign_apply(ovl_ctx *ctx, double *out, const double *in, double tol);
 
 /* out ~= D_N in = rho in + Gamma5 sign(Q) in (Eq. overlap_def), sign to accuracy tol. */
@@ -276,25 +302,58 @@ typedef struct {
 
 typedef struct {
     long launches;          /* kernels launched by the library since the last reset (all contexts) */
-    ovl_prof_kernel k[4];   /* 0: FP64 multishift stencils, 1: FP64 shift updates,
-                               2: FP32 multishift stencils, 3: FP32 shift updates */
+    ovl_prof_kernel k[6];   /* 0: FP64 multishift stencils, 1: FP64 shift updates,
+                               2: FP32 multishift stencils, 3: FP32 shift updates,
+                               4: float-float multishift stencils, 5: float-float shift updates */
     int valid;              /* 1 if every event timing could be read */
 } ovl_prof;
 
 /* Times reps back-to-back full-lattice Wilson stencil launches (out = D_W(m0_ker) in on
- * internal buffers, after 3 untimed launches) with CUDA events on the context's stream;
- * precision 0 = FP64, 1 = FP32. *ms = average milliseconds per launch. Algorithmic traffic
- * of one launch: 96 reals per site (4 links x 12, the input and the output spinor). */
+ * internal buffers filled with seeded pseudo-random values, after 3 untimed launches) with
+ * CUDA events on the context's stream; precision 0 = FP64, 1 = FP32, 2 = float-float.
+ * *ms = average milliseconds per launch. Algorithmic traffic of one launch: 96 reals per site
+ * (4 links x 12, the input and the output spinor). */
 ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms);
 
 /* As ovl_dslash_time for the multi-RHS stencil applied to nrhs (1..12) right-hand sides per
- * launch; *ms per launch (nrhs full-lattice applications). */
+ * launch (precision 0 = FP64, 1 = FP32); *ms per launch (nrhs full-lattice applications). */
 ovl_status ovl_dslash_time_n(ovl_ctx *ctx, int precision, int nrhs, int reps, double *ms);
+
+/* Measured fused multiply-add throughput of the current device in GFLOP/s (2 flops per FMA):
+ * precision 0 = FP64, 1 = FP32. Each thread runs independent FMA chains, 8 blocks of 256
+ * threads per SM, one launch of >= 20 ms timed with CUDA events after a warm-up launch. It is
+ * the ALU roofline denominator of the FP64 stencils (FP64) and of the float-float ones (FP32);
+ * instrumentation, not part of the paper's method. Allocates 16 bytes and one stream. */
+ovl_status ovl_fma_peak(int precision, double *gflops);
 
 /* on = 1 enables event timing (allocates a small history buffer), 0 disables it. */
 ovl_status ovl_prof_enable(ovl_ctx *ctx, int on);
 /* Reads the accumulated counters; reset = 1 zeroes them afterwards. */
 ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset);
+
+/* ---------------------------------------------------------------------------------
+ * Operators in a chosen arithmetic. The paper runs its preconditioner in single precision
+ * and the outer D_N products in double precision (Sec. 5.2, Sec. 5.3 and Table 3); these
+ * entry points apply the same operators as wilson_apply, wilson_apply_n and sign_apply in
+ * each arithmetic the solver uses (ovl_arith), so that every one of them can be checked
+ * against an FP64 reference on its own. Vectors are FP64 at the boundary (layout above);
+ * they are rounded to the requested arithmetic on entry and the result is returned in
+ * FP64. OVL_EINVAL for an arithmetic the operator does not have.
+ * --------------------------------------------------------------------------------- */
+
+/* out = D_W(m0) in (Eq. Wilson-Dirac) in arith = OVL_ARITH_FP64, OVL_ARITH_FF or OVL_ARITH_FP32,
+ * with the context's stencil variant (params.stencil_tps; float-float always 1 thread per site). */
+ovl_status wilson_apply_arith(ovl_ctx *ctx, double *out, const double *in, double m0, int arith);
+
+/* out_k = D_W(m0) in_k for k < n_rhs with the multi-RHS stencil (blocks of up to 12 right-hand
+ * sides per launch) in arith = OVL_ARITH_FP64 or OVL_ARITH_FP32. */
+ovl_status wilson_apply_n_arith(ovl_ctx *ctx, double *out, const double *in, int n_rhs, double m0, int arith);
+
+/* out ~= sign(Q) in to relative accuracy tol (Zolotarev + multishift CG, as sign_apply) in any
+ * ovl_arith. The accuracy each arithmetic can reach bounds the useful tol: float-float and FP64
+ * about 1e-12, FP32 about 1e-6, FP16-stored directions about 1e-3, BF16-stored about 1e-2 (the
+ * outer solver hands each arithmetic only requests above these floors). */
+ovl_status sign_apply_arith(ovl_ctx *ctx, double *out, const double *in, double tol, int arith);
 
 /* out = D_W(m0) in, the Wilson-Dirac operator of Eq. (Wilson-Dirac), for callers that cannot
  * allocate device memory. The paper has no counterpart to this entry point; it exists for
@@ -303,11 +362,17 @@ ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset);
  * context (ovl_create allocates) and calls no allocating routine.
  * out, in: V*12 complex doubles, gauge: V*4*9 complex doubles, all DEVICE memory in the
  * boundary layout above; dims as for ovl_create; antiperiodic: 1 = antiperiodic time boundary.
- * The links are taken as SU(3) without a check (row 2 is rebuilt from rows 0 and 1).
+ * All nine complex entries of every link are used as given; unlike ovl_create, no SU(3)
+ * check is made. The three pointers must be memory of the current device (or managed
+ * memory); pointers into another GPU are rejected with OVL_EINVAL. The library cannot see
+ * buffer sizes: out and in must hold V*12 and gauge V*4*9 complex doubles.
  * Working memory: one fixed device array inside the library of 16384 lattice sites
  * (about 15.7 MB), reserved on every GPU that loads the library until the process exits;
  * larger lattices are rejected with OVL_EINVAL. The first call on a device looks the
- * array's address up on that device (make this first call before any stream capture).
+ * array's address up on that device (make this first call before any stream capture) and
+ * keeps it for the life of the process: it belongs to the device's primary context, so
+ * after cudaDeviceReset, or with another driver context current, the kept address is stale
+ * and this entry point must not be called again in that process.
  * All calls share the array: calls whose work overlaps on the GPU (other streams, other
  * host threads) race and give undefined results; calls ordered on one stream are safe.
  * The work is enqueued on cuda_stream (NULL = the legacy default stream) and the call

@@ -20,6 +20,7 @@ OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ENOCONV, OVL_EBREAKDOWN, OVL_ETIMEOUT, OVL_E
 OVL_FP64, OVL_MIXED_FP32, OVL_MIXED_HALF, OVL_MIXED_BF16 = range(4)
 OVL_PREC_NONE, OVL_PREC_WILSON, OVL_PREC_RECURSIVE = range(3)
 OVL_SIGN_ZOLOTAREV, OVL_SIGN_KRYLOV = range(2)
+OVL_ARITH_FP64, OVL_ARITH_FF, OVL_ARITH_FP32, OVL_ARITH_FP16, OVL_ARITH_BF16 = range(5)
 _STATUS = {0: "OVL_OK", 1: "OVL_EINVAL", 2: "OVL_ENOMEM", 3: "OVL_ENOCONV", 4: "OVL_EBREAKDOWN",
            5: "OVL_ETIMEOUT", 6: "OVL_ECUDA"}
 
@@ -46,7 +47,7 @@ class ovl_params(ctypes.Structure):
         ("use_graphs", ctypes.c_int), ("check_every", ctypes.c_int), ("stencil_tps", ctypes.c_int),
         ("sap_tps", ctypes.c_int), ("adaptive_poles", ctypes.c_int), ("n_deflate", ctypes.c_int),
         ("deflate_tol", ctypes.c_double), ("sign_method", ctypes.c_int), ("krylov_m", ctypes.c_int),
-        ("krylov_keep", ctypes.c_int),
+        ("krylov_keep", ctypes.c_int), ("ff_outer", ctypes.c_int), ("max_seconds", ctypes.c_double),
     ]
 
 
@@ -56,7 +57,7 @@ class ovl_stats(ctypes.Structure):
         ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("ms_iters_fp64", ctypes.c_long),
         ("ms_iters_low", ctypes.c_long), ("prec_iters", ctypes.c_long), ("true_rel_resid", ctypes.c_double),
         ("seconds", ctypes.c_double), ("t_sign_fp64", ctypes.c_double), ("t_sign_low", ctypes.c_double),
-        ("t_prec", ctypes.c_double),
+        ("t_prec", ctypes.c_double), ("ms_iters_ff", ctypes.c_long),
     ]
 
     def as_dict(self):
@@ -89,12 +90,13 @@ class ovl_prof_kernel(ctypes.Structure):
                 ("flops", ctypes.c_double), ("timed", ctypes.c_long), ("timed_bytes", ctypes.c_double)]
 
 
-PROF_KERNELS = ["ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_f32"]
+PROF_KERNELS = ["ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_f32", "ms_stencil_ff",
+                "ms_shifts_ff"]
 
 
 class ovl_prof(ctypes.Structure):
     """Mirror of ovl_prof (instrumentation counters)."""
-    _fields_ = [("launches", ctypes.c_long), ("k", ovl_prof_kernel * 4), ("valid", ctypes.c_int)]
+    _fields_ = [("launches", ctypes.c_long), ("k", ovl_prof_kernel * 6), ("valid", ctypes.c_int)]
 
     def as_dict(self):
         d = {"launches": self.launches, "valid": self.valid}
@@ -107,7 +109,7 @@ class ovl_prof(ctypes.Structure):
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
            "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "ovl_request_bytes", "wilson_sap_apply", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
-           "ovl_apply_n", "ovl_dslash_time_n", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
+           "ovl_apply_n", "ovl_dslash_time_n", "wilson_apply_arith", "wilson_apply_n_arith", "sign_apply_arith", "ovl_fma_peak", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
 _lib = None
@@ -148,6 +150,10 @@ def lib():
         L.wilson_apply_n.argtypes = [P, P, P, I_, D]
         L.ovl_apply_n.argtypes = [P, P, P, I_, D]
         L.ovl_dslash_time_n.argtypes = [P, I_, I_, I_, ctypes.POINTER(D)]
+        L.wilson_apply_arith.argtypes = [P, P, P, D, I_]
+        L.wilson_apply_n_arith.argtypes = [P, P, P, I_, D, I_]
+        L.sign_apply_arith.argtypes = [P, P, P, D, I_]
+        L.ovl_fma_peak.argtypes = [I_, ctypes.POINTER(D)]
         L.ovl_server_create.argtypes = [ctypes.POINTER(P), I_, ctypes.c_size_t]
         L.ovl_server_submit.argtypes = [P, ctypes.POINTER(ovl_request), ctypes.POINTER(ctypes.c_long)]
         L.ovl_server_query.argtypes = [P, ctypes.c_long, ctypes.POINTER(ovl_result)]
@@ -238,6 +244,24 @@ def sign_apply(ctx, out, inp, tol):
     return out
 
 
+def wilson_apply_arith(ctx, out, inp, m0, arith):
+    """out = D_W(m0) inp in the arithmetic `arith` (OVL_ARITH_FP64, OVL_ARITH_FF or OVL_ARITH_FP32)."""
+    _check(lib().wilson_apply_arith(ctx, _ptr(out, True), _ptr(inp), float(m0), int(arith)), ctx)
+    return out
+
+
+def wilson_apply_n_arith(ctx, out, inp, n_rhs, m0, arith):
+    """out_k = D_W(m0) inp_k with the multi-RHS stencil in OVL_ARITH_FP64 or OVL_ARITH_FP32."""
+    _check(lib().wilson_apply_n_arith(ctx, _ptr(out, True), _ptr(inp), int(n_rhs), float(m0), int(arith)), ctx)
+    return out
+
+
+def sign_apply_arith(ctx, out, inp, tol, arith):
+    """out ~= sign(Q) inp to accuracy tol in any ovl_arith (FP64, FF, FP32, FP16- or BF16-stored)."""
+    _check(lib().sign_apply_arith(ctx, _ptr(out, True), _ptr(inp), float(tol), int(arith)), ctx)
+    return out
+
+
 def ovl_apply(ctx, out, inp, tol):
     """out ~= D_N inp = rho inp + Gamma5 sign(Q) inp (Eq. overlap_def), sign to accuracy tol."""
     _check(lib().ovl_apply(ctx, _ptr(out, True), _ptr(inp), float(tol)), ctx)
@@ -256,7 +280,22 @@ def ovl_solve(ctx, x, b, n_rhs=1, tol=0.0, check=True):
 def wilson_apply_noalloc(out, inp, gauge, dims, m0, antiperiodic=True, stream=None):
     """out = D_W(m0) inp without a context and without device allocation (device tensors only).
 
-    Returns once the work is enqueued on `stream` (default: the legacy default stream)."""
+    The C entry point cannot see buffer sizes, so the sizes, dtype, layout and device of the
+    three tensors are checked here before the call. Returns once the work is enqueued on
+    `stream` (default: the legacy default stream)."""
+    V = int(math.prod(int(x) for x in dims))
+    for name, t, n in (("out", out, V * 12), ("inp", inp, V * 12), ("gauge", gauge, V * 36)):
+        if hasattr(t, "data_ptr"):
+            import torch
+            if t.dtype != torch.complex128 or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous complex128 tensor" % name)
+            if t.numel() < n:
+                raise ValueError("%s holds %d complex numbers, needs %d" % (name, t.numel(), n))
+            if t.is_cuda and t.device.index != torch.cuda.current_device():
+                raise ValueError("%s is on cuda:%d, the current device is cuda:%d"
+                                 % (name, t.device.index, torch.cuda.current_device()))
+        elif getattr(t, "size", n) < n:
+            raise ValueError("%s holds %d complex numbers, needs %d" % (name, t.size, n))
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
     _check(lib().wilson_apply_noalloc(_ptr(out, True), _ptr(inp), _ptr(gauge), ctypes.cast(d, ctypes.c_void_p),
                                       float(m0), int(bool(antiperiodic)),
@@ -340,7 +379,8 @@ def ovl_tuning_sap(ctx):
 
 
 def ovl_dslash_time(ctx, precision, reps=20):
-    """Average ms of one full-lattice Wilson stencil launch (precision 0 = FP64, 1 = FP32)."""
+    """Average ms of one full-lattice Wilson stencil launch (precision 0 = FP64, 1 = FP32,
+    2 = float-float) on a seeded random input."""
     ms = ctypes.c_double()
     _check(lib().ovl_dslash_time(ctx, int(precision), int(reps), ctypes.byref(ms)), ctx)
     return ms.value
@@ -363,6 +403,13 @@ def ovl_dslash_time_n(ctx, precision, nrhs, reps=20):
     ms = ctypes.c_double()
     _check(lib().ovl_dslash_time_n(ctx, int(precision), int(nrhs), int(reps), ctypes.byref(ms)), ctx)
     return ms.value
+
+
+def fma_peak(precision):
+    """Measured FMA throughput of the current GPU in GFLOP/s (precision 0 = FP64, 1 = FP32)."""
+    g = ctypes.c_double()
+    _check(lib().ovl_fma_peak(int(precision), ctypes.byref(g)))
+    return g.value
 
 
 def ovl_info(ctx):
@@ -412,6 +459,15 @@ class Overlap:
 
     def ovl_apply(self, out, inp, tol):
         return ovl_apply(self.ctx, out, inp, tol)
+
+    def wilson_apply_arith(self, out, inp, m0, arith):
+        return wilson_apply_arith(self.ctx, out, inp, m0, arith)
+
+    def wilson_apply_n_arith(self, out, inp, n_rhs, m0, arith):
+        return wilson_apply_n_arith(self.ctx, out, inp, n_rhs, m0, arith)
+
+    def sign_apply_arith(self, out, inp, tol, arith):
+        return sign_apply_arith(self.ctx, out, inp, tol, arith)
 
     def ovl_solve(self, x, b, n_rhs=1, tol=0.0, check=True):
         return ovl_solve(self.ctx, x, b, n_rhs, tol, check)

@@ -72,6 +72,8 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->sign_method = OVL_SIGN_ZOLOTAREV;
     p->krylov_m = 40;
     p->krylov_keep = 8;
+    p->ff_outer = 1;
+    p->max_seconds = 0.0;
     return OVL_OK;
 }
 
@@ -102,6 +104,8 @@ static ovl_status validate_params(const ovl_params &p, const int L[4], std::stri
     if (p.sign_method != OVL_SIGN_ZOLOTAREV && p.sign_method != OVL_SIGN_KRYLOV) { err = "sign_method must be 0 or 1"; return OVL_EINVAL; }
     if (p.krylov_m < 4 || p.krylov_m > 120) { err = "krylov_m must be in [4,120]"; return OVL_EINVAL; }
     if (p.krylov_keep < 0 || p.krylov_keep > p.krylov_m - 2) { err = "krylov_keep must be in [0, krylov_m - 2]"; return OVL_EINVAL; }
+    if (p.ff_outer != 0 && p.ff_outer != 1) { err = "ff_outer must be 0 or 1"; return OVL_EINVAL; }
+    if (!(p.max_seconds >= 0)) { err = "max_seconds must be >= 0"; return OVL_EINVAL; }
     for (int m = 0; m < 4 && p.precond != OVL_PREC_NONE; m++) {
         if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m]) {
             err = "sap_block must be even and divide the lattice extent";
@@ -143,7 +147,7 @@ Ctx::~Ctx() {
     if (stream) cudaStreamSynchronize(stream);
     for (auto &gr : graphs)
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
-    for (int w = 0; w < 2; w++)
+    for (int w = 0; w < 3; w++)
         if (ev_ready[w])
             for (int k = 0; k < 4; k++) cudaEventDestroy(ev[w][k]);
     for (void *p : allocs) cudaFree(p);
@@ -279,7 +283,7 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes
     Ctx *c = this;
     const int chunk = std::min(p.check_every, kMaxChunk);
     const int sample = chunk / 2;   // the iteration of every chunk whose kernels are timed
-    const double rbytes = which == 0 ? 8.0 : 4.0;
+    const double rbytes = which == 1 ? 4.0 : 8.0;   // bytes per real: FP32 slot 4, FP64 and float-float 8
     int done_iters = 0, iter_before = 0;
     GraphSlot &gs = graphs[slot];
     if (prof && !ev_ready[which]) {
@@ -352,6 +356,7 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes
             err = "multishift CG breakdown (non-finite or non-positive scalar)";
             return OVL_EBREAKDOWN;
         }
+        if (!done && past_deadline()) return OVL_ETIMEOUT;
         if (done) {
             *iters_out = iter;
             return OVL_OK;
@@ -384,17 +389,95 @@ ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
     CK(ms_init_f64(g, n, ms64_state, ms64, bm, rs, stream));
     int iters = 0;
     auto fn = [&](cudaEvent_t *e, unsigned f) { return ms_iter_f64(g, U64, m0_ker, ms64_state, ms64, rs, stream, e, f); };
-    ST(ms_run(ms64_state, 0, 0, 48.0 * 8.0, fn, &iters));
+    // at the iteration cap the output is still formed from the last iterate (status ENOCONV)
+    const ovl_status ms = ms_run(ms64_state, 0, 0, 48.0 * 8.0, fn, &iters);
+    if (ms != OVL_OK && ms != OVL_ENOCONV) return ms;
     stat_ms64 += iters;
     const double sc = zs_d0[n - 1] / lam_min;
     if (mode == 0) CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 1, sc, nullptr, 0.0, stream));
     else CK(wilson_f64(g, U64, ms64.y, out, m0_ker, 0, sc, b, rho, stream));
     if (ndefl) ST(defl_add64(dc, out, mode));
+    return ms;
+}
+
+// y = b + sum_l w_l (Q^2+sigma_l)^{-1} b in float-float arithmetic (ff.cuh) on the FP32
+// pipes, for the sign applications that need FP64 accuracy; b, out are FP64 even-odd
+// spinors and the result has the same form as sign64's. The multishift vectors and links
+// are float-float; the Zolotarev coefficients and the CG scalars stay FP64 on the device.
+ovl_status Ctx::sign_ff(const double2 *b, double2 *out, double tol, int mode) {
+    if (p.sign_method == OVL_SIGN_KRYLOV) return sign64_krylov(b, out, tol, mode);
+    PhaseClock pclk(this, &t_sign64);
+    Ctx *c = this;
+    ST(ensure_msff());
+    std::vector<double> dc;
+    const double2 *bm = b;
+    if (ndefl) {
+        ST(defl_project64(b, defl_tmp64, dc));
+        bm = defl_tmp64;
+    }
+    const long words = (long)g.V * 12;
+    int n;
+    ST(ms_setup(msff_state, tol, &n));
+    // b in float-float into t (t is overwritten by the first iteration's Q p)
+    CK(dev_d2ff(bm, msff.t, words, stream));
+    CK(ms_init_ff(g, n, msff_state, msff, msff.t, rs, stream));
+    int iters = 0;
+    auto fn = [&](cudaEvent_t *e, unsigned f) { return ms_iter_ff(g, Uff, m0_ker, msff_state, msff, rs, stream, e, f); };
+    const ovl_status ms = ms_run(msff_state, 2, 5, 48.0 * 8.0, fn, &iters);
+    if (ms != OVL_OK && ms != OVL_ENOCONV) return ms;
+    stat_msff += iters;
+    const double sc = zs_d0[n - 1] / lam_min;
+    // s = (d0/lmin) [gamma5] D_W y in float-float, then FP64; D_N b = rho b + s without gamma5
+    CK(wilson_ff(g, Uff, msff.y, msff.t, m0_ker, mode == 0, sc, nullptr, 0.0, stream));
+    CK(dev_ff2d(msff.t, out, words, stream));
+    if (mode == 1) CK(dev_axpby(rho, (const double *)b, 1.0, (double *)out, 2 * words, stream));
+    if (ndefl) ST(defl_add64(dc, out, mode));
+    return ms;
+}
+
+ovl_status Ctx::ensure_ff_links() {
+    Ctx *c = this;
+    if (Uff) return OVL_OK;
+    const long words = (long)g.V * 4 * kLink64Words;
+    ST(alloc((void **)&Uff, (size_t)words * sizeof(ffw)));
+    CK(dev_d2ff(U64, Uff, words, stream));
+    return OVL_OK;
+}
+
+ovl_status Ctx::ensure_msff() {
+    ST(ensure_ff_links());
+    if (msff.p) return OVL_OK;
+    void *buf;
+    if (!msff_state) {
+        ST(alloc(&buf, sizeof(MsState)));
+        msff_state = (MsState *)buf;
+    }
+    const long words = (long)g.V * 12;   // ffw per vector
+    ST(alloc(&buf, (size_t)words * sizeof(ffw) * (npole + 3)));
+    ffw *f = (ffw *)buf;
+    msff.r = f;
+    msff.t = f + words;
+    msff.y = f + 2 * words;
+    msff.p = f + 3 * words;
+    msff.stride = words;
+    return OVL_OK;
+}
+
+ovl_status Ctx::sign_outer(const double2 *b, double2 *out, double tol, int mode) {
+    if (p.precision != OVL_FP64 && p.ff_outer) return sign_ff(b, out, tol, mode);
+    return sign64(b, out, tol, mode);
+}
+
+ovl_status Ctx::sign_outer_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode) {
+    if (!(p.precision != OVL_FP64 && p.ff_outer)) return sign64_batch(b, out, nrhs, tol, mode);
+    const long w = (long)g.V * 12;   // float-float: one right-hand side at a time
+    for (int y = 0; y < nrhs; y++)
+        if (tol[y] > 0) ST(sign_ff(b + y * w, out + y * w, tol[y], mode));
     return OVL_OK;
 }
 
 // FP32 version for the inner (low-accuracy) D_N: b, out FP32 eo spinors.
-ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
+ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode, int store) {
     PhaseClock pclk(this, &t_sign_low);
     Ctx *c = this;
     int iters = 0, n = npole;
@@ -405,16 +488,19 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
         ST(defl_project32(b, defl_tmp32, dc));
         b = defl_tmp32;
     }
-    if (p.precision == OVL_MIXED_HALF || p.precision == OVL_MIXED_BF16) {
+    if (store < 0) store = p.precision == OVL_MIXED_HALF ? 1 : p.precision == OVL_MIXED_BF16 ? 2 : 0;
+    ovl_status ms = OVL_OK;
+    if (store != 0) {
         // shifted directions stored in 16 bits (per site: 48 B, + 4 B norm for FP16, read and written)
-        const bool bf = p.precision == OVL_MIXED_BF16;
+        const bool bf = store == 2;
         ST(ensure_msh());
         ST(ms_setup(msh_state, tol, &n));
         CK(ms_init_half(g, n, msh_state, msh, b, rs, bf, stream));
         auto fn = [&](cudaEvent_t *e, unsigned f) {
             return ms_iter_half(g, U32, (float)m0_ker, msh_state, msh, rs, bf, stream, e, f);
         };
-        ST(ms_run(msh_state, 1, 2, bf ? 96.0 : 104.0, fn, &iters));
+        ms = ms_run(msh_state, 1, bf ? 6 : 2, bf ? 96.0 : 104.0, fn, &iters);
+        if (ms != OVL_OK && ms != OVL_ENOCONV) return ms;
         y = msh.y;
     } else {
         ST(ensure_ms32());
@@ -423,7 +509,8 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
         auto fn = [&](cudaEvent_t *e, unsigned f) {
             return ms_iter_f32(g, U32, (float)m0_ker, ms32_state, ms32, rs, stream, e, f);
         };
-        ST(ms_run(ms32_state, 1, 1, 48.0 * 4.0, fn, &iters));
+        ms = ms_run(ms32_state, 1, 1, 48.0 * 4.0, fn, &iters);
+        if (ms != OVL_OK && ms != OVL_ENOCONV) return ms;
         y = ms32.y;
     }
     stat_ms32 += iters;
@@ -431,7 +518,7 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode) {
     if (mode == 0) CK(wilson_f32(g, U32, y, out, (float)m0_ker, 1, sc, nullptr, 0.f, stream));
     else CK(wilson_f32(g, U32, y, out, (float)m0_ker, 0, sc, b_orig, (float)rho, stream));
     if (ndefl) ST(defl_add32(dc, out, mode));
-    return OVL_OK;
+    return ms;
 }
 
 ovl_status Ctx::ensure_ms64() {
@@ -524,6 +611,7 @@ ovl_status Ctx::msb_run(int nrhs, const double *tol, int n, int slot, Init init_
             all = all && h[2];
             itmax = std::max(itmax, (long)h[1]);
         }
+        if (!all && past_deadline()) return OVL_ETIMEOUT;
         if (all) {
             *iters_out = itmax;
             return OVL_OK;
@@ -1139,8 +1227,10 @@ extern "C" ovl_status sign_apply(ovl_ctx *ctx, double *out, const double *in, do
     ST(check_ctx_ptrs(c, out, in));
     ST(check_tol(c, tol));
     ST(c->import_vec(in, c->io_a));
-    ST(c->sign64(c->io_a, c->io_b, tol, 0));
-    return c->export_vec(c->io_b, out);
+    const ovl_status st = c->sign64(c->io_a, c->io_b, tol, 0);
+    if (st != OVL_OK && st != OVL_ENOCONV) return st;
+    ST(c->export_vec(c->io_b, out));
+    return st;
 }
 
 extern "C" ovl_status ovl_apply(ovl_ctx *ctx, double *out, const double *in, double tol) {
@@ -1148,8 +1238,10 @@ extern "C" ovl_status ovl_apply(ovl_ctx *ctx, double *out, const double *in, dou
     ST(check_ctx_ptrs(c, out, in));
     ST(check_tol(c, tol));
     ST(c->import_vec(in, c->io_a));
-    ST(c->sign64(c->io_a, c->io_b, tol, 1));
-    return c->export_vec(c->io_b, out);
+    const ovl_status st = c->sign64(c->io_a, c->io_b, tol, 1);
+    if (st != OVL_OK && st != OVL_ENOCONV) return st;
+    ST(c->export_vec(c->io_b, out));
+    return st;
 }
 
 extern "C" ovl_status ovl_solve(ovl_ctx *ctx, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats) {
@@ -1182,7 +1274,7 @@ extern "C" ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset) {
     out->launches = launches_total() - c->launch_mark;
     out->valid = 1;
     const double V = (double)c->g.V;
-    for (int w = 0; w < 2; w++) {
+    for (int w = 0; w < 3; w++) {
         const ProfAcc &pa = c->pacc[w];
         ovl_prof_kernel &st = out->k[2 * w], &sh = out->k[2 * w + 1];
         st.ms = pa.q_ms + pa.r_ms;
@@ -1199,8 +1291,7 @@ extern "C" ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset) {
         if (!pa.valid) out->valid = 0;
     }
     if (reset) {
-        c->pacc[0] = ProfAcc();
-        c->pacc[1] = ProfAcc();
+        for (int w = 0; w < 3; w++) c->pacc[w] = ProfAcc();
         c->launch_mark = launches_total();
     }
     return OVL_OK;
@@ -1311,12 +1402,136 @@ extern "C" ovl_status wilson_sap_apply(ovl_ctx *ctx, double *out, const double *
     return c->export_vec(c->io_b, out);
 }
 
+// ------------------------------------------------------------------ operators in a chosen arithmetic
+static bool arith_ok(int a, bool sign) {
+    return a == OVL_ARITH_FP64 || a == OVL_ARITH_FF || a == OVL_ARITH_FP32 ||
+           (sign && (a == OVL_ARITH_FP16 || a == OVL_ARITH_BF16));
+}
+
+extern "C" ovl_status wilson_apply_arith(ovl_ctx *ctx, double *out, const double *in, double m0, int arith) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    if (!isfinite(m0) || !arith_ok(arith, false)) {
+        c->err = "wilson_apply_arith: need finite m0 and arith OVL_ARITH_FP64, OVL_ARITH_FF or OVL_ARITH_FP32";
+        return OVL_EINVAL;
+    }
+    ST(c->import_vec(in, c->io_a));
+    const long w = (long)c->g.V * 12;
+    if (arith == OVL_ARITH_FP64) {
+        CK(wilson_f64(c->g, c->U64, c->io_a, c->io_b, m0, 0, 1.0, nullptr, 0.0, c->stream));
+    } else if (arith == OVL_ARITH_FF) {
+        ST(c->ensure_msff());
+        CK(dev_d2ff(c->io_a, c->msff.t, w, c->stream));
+        CK(wilson_ff(c->g, c->Uff, c->msff.t, c->msff.y, m0, 0, 1.0, nullptr, 0.0, c->stream));
+        CK(dev_ff2d(c->msff.y, c->io_b, w, c->stream));
+    } else {
+        ST(ensure_f32_buffers(c));
+        CK(spinor_d2f(c->g, c->io_a, (float4 *)c->f_a, c->stream));
+        CK(wilson_f32(c->g, c->U32, (const float4 *)c->f_a, (float4 *)c->f_b, (float)m0, 0, 1.f, nullptr, 0.f,
+                      c->stream));
+        CK(spinor_f2d(c->g, (const float4 *)c->f_b, c->io_b, c->stream));
+    }
+    return c->export_vec(c->io_b, out);
+}
+
+extern "C" ovl_status wilson_apply_n_arith(ovl_ctx *ctx, double *out, const double *in, int n_rhs, double m0,
+                                           int arith) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    if (arith == OVL_ARITH_FP64) return wilson_apply_n(ctx, out, in, n_rhs, m0);
+    if (n_rhs < 1 || !isfinite(m0) || arith != OVL_ARITH_FP32) {
+        c->err = "wilson_apply_n_arith: need n_rhs >= 1, finite m0 and arith OVL_ARITH_FP64 or OVL_ARITH_FP32";
+        return OVL_EINVAL;
+    }
+    const int blk = std::min(kMaxBatch, n_rhs);
+    if (!c->xbat || c->xbat_cap < blk) {
+        void *buf;
+        ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2 * blk));
+        c->xbat = (double2 *)buf;
+        c->bbat = c->xbat + (size_t)blk * c->g.V * 12;
+        c->xbat_cap = blk;
+    }
+    if (!c->fbat || c->fbat_cap < blk) {
+        void *buf;
+        ST(c->alloc(&buf, (size_t)c->n64 * sizeof(float) * 2 * blk));
+        c->fbat = (float *)buf;
+        c->fbat_cap = blk;
+    }
+    const long w = (long)c->g.V * 12, wf = (long)c->g.V * 6;
+    float4 *fa = (float4 *)c->fbat, *fb = fa + (size_t)blk * wf;
+    for (int r0 = 0; r0 < n_rhs; r0 += blk) {
+        const int nb = std::min(blk, n_rhs - r0);
+        for (int y = 0; y < nb; y++) ST(c->import_vec(in + (size_t)(r0 + y) * c->n64, c->bbat + y * w));
+        CK(spinor_d2f_n(c, c->bbat, fa, nb));
+        CK(wilson_batch_f32(c->g, c->U32, fa, fb, wf, nb, (float)m0, 0, 1.f, nullptr, 0.f, c->stream));
+        CK(spinor_f2d_n(c, fb, c->xbat, nb));
+        for (int y = 0; y < nb; y++) ST(c->export_vec(c->xbat + y * w, out + (size_t)(r0 + y) * c->n64));
+    }
+    return OVL_OK;
+}
+
+extern "C" ovl_status sign_apply_arith(ovl_ctx *ctx, double *out, const double *in, double tol, int arith) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    ST(check_ctx_ptrs(c, out, in));
+    ST(check_tol(c, tol));
+    if (!arith_ok(arith, true)) {
+        c->err = "sign_apply_arith: arith must be an ovl_arith value";
+        return OVL_EINVAL;
+    }
+    ST(c->import_vec(in, c->io_a));
+    ovl_status st;
+    if (arith == OVL_ARITH_FP64) {
+        st = c->sign64(c->io_a, c->io_b, tol, 0);
+    } else if (arith == OVL_ARITH_FF) {
+        st = c->sign_ff(c->io_a, c->io_b, tol, 0);
+    } else {
+        ST(ensure_f32_buffers(c));
+        CK(spinor_d2f(c->g, c->io_a, (float4 *)c->f_a, c->stream));
+        st = c->sign32((const float4 *)c->f_a, (float4 *)c->f_b, tol, 0,
+                       arith == OVL_ARITH_FP16 ? 1 : arith == OVL_ARITH_BF16 ? 2 : 0);
+        if (st == OVL_OK || st == OVL_ENOCONV) CK(spinor_f2d(c->g, (const float4 *)c->f_b, c->io_b, c->stream));
+    }
+    if (st != OVL_OK && st != OVL_ENOCONV) return st;
+    ST(c->export_vec(c->io_b, out));
+    return st;
+}
+
+// Seeded pseudo-random fill of n floats in [-1, 1) (a counter hash per element), so that
+// the stencil timings run on data of the magnitude of a real field and not on zeros.
+__global__ void k_fill_random(float *x, long n, unsigned seed) {
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)k * 2654435761u ^ seed;
+        h ^= h >> 16;
+        h *= 0x7feb352du;
+        h ^= h >> 15;
+        h *= 0x846ca68bu;
+        h ^= h >> 16;
+        x[k] = (float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f;
+    }
+}
+static cudaError_t fill_random(void *buf, size_t bytes, cudaStream_t st) {
+    const long n = (long)(bytes / sizeof(float));
+    k_fill_random<<<std::min<long>(4096, (n + kBlock - 1) / kBlock), kBlock, 0, st>>>((float *)buf, n, 0x9e3779b9u);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
-    if (!c || !ms || reps < 1 || (precision != 0 && precision != 1)) return OVL_EINVAL;
+    if (!c || !ms || reps < 1 || precision < 0 || precision > 2) return OVL_EINVAL;
+    if (precision == 2) ST(c->ensure_ff_links());
     void *buf;
     ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2));
-    CK(cudaMemsetAsync(buf, 0, (size_t)c->n64 * sizeof(double) * 2, c->stream));
+    // random input spinor (floats reinterpreted: FP64 words become finite values of
+    // moderate exponent, FP32 and float-float words values in [-1, 1))
+    if (precision == 0) {
+        CK(fill_random(buf, (size_t)c->n64 * sizeof(double), c->stream));
+        CK(spinor_f2d(c->g, (const float4 *)buf, (double2 *)buf + (size_t)c->g.V * 12, c->stream));
+        CK(cudaMemcpyAsync(buf, (double2 *)buf + (size_t)c->g.V * 12, (size_t)c->n64 * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        CK(fill_random(buf, (size_t)c->n64 * sizeof(double) * 2, c->stream));
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1327,6 +1542,9 @@ extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, dou
         if (precision == 0)
             e = wilson_f64(c->g, c->U64, (const double2 *)buf, (double2 *)buf + (size_t)c->g.V * 12, c->m0_ker, 0, 1.0,
                            nullptr, 0.0, c->stream);
+        else if (precision == 2)
+            e = wilson_ff(c->g, c->Uff, (const ffw *)buf, (ffw *)buf + (size_t)c->g.V * 12, c->m0_ker, 0, 1.0, nullptr,
+                          0.0, c->stream);
         else
             e = wilson_f32(c->g, c->U32, (const float4 *)buf, (float4 *)buf + (size_t)c->g.V * 6, (float)c->m0_ker, 0,
                            1.f, nullptr, 0.f, c->stream);
@@ -1412,7 +1630,15 @@ extern "C" ovl_status ovl_dslash_time_n(ovl_ctx *ctx, int precision, int nrhs, i
     void *buf;
     const size_t bytes = (size_t)c->n64 * (precision == 0 ? 8 : 4) * nrhs * 2;
     ST(c->alloc(&buf, bytes));
-    CK(cudaMemsetAsync(buf, 0, bytes, c->stream));
+    if (precision == 0) {   // FP64 random values: FP32 random words converted, one vector at a time
+        const long w = (long)c->g.V * 12;
+        CK(fill_random(buf, (size_t)c->n64 * sizeof(double), c->stream));
+        for (int y = 1; y < 2 * nrhs; y++)
+            CK(spinor_f2d(c->g, (const float4 *)buf, (double2 *)buf + y * w, c->stream));
+        CK(cudaMemcpyAsync(buf, (double2 *)buf + w, (size_t)w * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        CK(fill_random(buf, bytes, c->stream));
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

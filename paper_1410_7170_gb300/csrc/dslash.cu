@@ -261,4 +261,43 @@ cudaError_t wilson_f32(const Geom &g, const float4 *U, const float4 *in, float4 
     return cudaGetLastError();
 }
 
+cudaError_t wilson_ff(const Geom &g, const ffw *U, const ffw *in, ffw *out, double m0, int g5, double a,
+                      const ffw *z, double b, cudaStream_t st) {
+    const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<ff>::value, 1 << 30);
+    k_wilson<ff, ffw, ffw><<<ls.grid, ls.block, 0, st>>>(g, U, in, out, ff(m0 + 4.0), g5, ff(a), z, ff(b), ls.spb);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ float-float conversion
+// double2 word k <-> ffw word k: hi = fl32(x), lo = fl32(x - hi) per real; back, hi + lo in FP64.
+__global__ void k_d2ff(const double2 *__restrict__ x, ffw *__restrict__ y, long n) {
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const double2 v = x[k];
+        const ff re(v.x), im(v.y);
+        reinterpret_cast<float4 *>(y)[k] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+}
+__global__ void k_ff2d(const ffw *__restrict__ x, double2 *__restrict__ y, long n) {
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const float4 v = reinterpret_cast<const float4 *>(x)[k];
+        y[k] = make_double2(ff(v.x, v.y).to_double(), ff(v.z, v.w).to_double());
+    }
+}
+static int conv_grid(long n) {
+    long b = (n + kBlock - 1) / kBlock;
+    const long cap = 16L * device_sm_count();
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+cudaError_t dev_d2ff(const double2 *x, ffw *y, long n, cudaStream_t st) {
+    k_d2ff<<<conv_grid(n), kBlock, 0, st>>>(x, y, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t dev_ff2d(const ffw *x, double2 *y, long n, cudaStream_t st) {
+    k_ff2d<<<conv_grid(n), kBlock, 0, st>>>(x, y, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace ovl

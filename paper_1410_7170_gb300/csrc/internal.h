@@ -7,6 +7,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace ovl {
 
@@ -28,6 +29,7 @@ struct RedScratch {
 template <typename R> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<double> { static constexpr int value = 2; };
 template <> struct MinBlocks<float> { static constexpr int value = 2; };
+template <> struct MinBlocks<ff> { static constexpr int value = 2; };
 
 // SMs of the current device (queried once per device and cached).
 int device_sm_count();
@@ -87,6 +89,13 @@ cudaError_t wilson_f64(const Geom &g, const double2 *U, const double2 *in, doubl
                        double a, const double2 *z, double b, cudaStream_t st);
 cudaError_t wilson_f32(const Geom &g, const float4 *U, const float4 *in, float4 *out, float m0, int g5,
                        float a, const float4 *z, float b, cudaStream_t st);
+// float-float stencil (one thread per site); links in the float-float layout of ff.cuh
+cudaError_t wilson_ff(const Geom &g, const ffw *U, const ffw *in, ffw *out, double m0, int g5, double a,
+                      const ffw *z, double b, cudaStream_t st);
+// FP64 <-> float-float conversion of n complex words (double2 <-> ffw, same word order; used
+// for even-odd spinors and for the FP64 link array)
+cudaError_t dev_d2ff(const double2 *x, ffw *y, long n, cudaStream_t st);
+cudaError_t dev_ff2d(const ffw *x, double2 *y, long n, cudaStream_t st);
 
 // ---------------------------------------------------------------- BLAS-1 (flat arrays of n doubles)
 // Reductions return through device memory `res` (written by the last block).
@@ -182,6 +191,11 @@ cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, Ms
                         RedScratch rs, cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
 cudaError_t ms_init_half(const Geom &g, int n, MsState *s, MsVectorsH v, const float4 *b, RedScratch rs, bool bf16,
                          cudaStream_t st);
+// float-float multishift (the FP64-accuracy sign on the FP32 pipes)
+cudaError_t ms_init_ff(const Geom &g, int n, MsState *s, MsVectors<ffw> v, const ffw *b, RedScratch rs,
+                       cudaStream_t st);
+cudaError_t ms_iter_ff(const Geom &g, const ffw *U, double m0, MsState *s, MsVectors<ffw> v, RedScratch rs,
+                       cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
 cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, MsVectorsH v, RedScratch rs, bool bf16,
                          cudaStream_t st, cudaEvent_t *ev = nullptr, unsigned ev_flags = 0);
 

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, co
                                                  const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs,
                                                  int spb) {
     if (s->done) return;
-    R v[1] = {0};   // per-thread sums in R; FP64 from the warp sums on (grid_reduce)
+    R v[1] = {R(0)};   // per-thread sums in R; FP64 from the warp sums on (grid_reduce)
     const bool lane_has_sites = threadIdx.x < spb;
     for (int k = blockIdx.x * spb + threadIdx.x; lane_has_sites && k < g.V; k += gridDim.x * spb) {
         int p, i;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, co
         wilson_combine<R>(m4, own, hop, res);
         apply_g5(res);
         store_spinor<R>(t, g.Vh, p, i, res);
-        R a0 = 0;   // per-site sums in the arithmetic type, across sites in FP64
+        R a0 = R(0);   // per-site sums in the arithmetic type, across sites in FP64
 #pragma unroll
         for (int c = 0; c < 12; c++) a0 += norm2(res[c]);
         v[0] += a0;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r(Geom g, co
                                                  ST *__restrict__ r, RedScratch rs, int spb) {
     if (s->done) return;
     const R alpha = (R)s->alpha, sig0 = (R)s->sigma[0];
-    R v[1] = {0};
+    R v[1] = {R(0)};
     const bool lane_has_sites = threadIdx.x < spb;
     for (int k = blockIdx.x * spb + threadIdx.x; lane_has_sites && k < g.V; k += gridDim.x * spb) {
         int p, i;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r(Geom g, co
         apply_g5(res);
         load_spinor<R>(p0, g.Vh, p, i, pp);
         load_spinor<R>(r, g.Vh, p, i, rv);
-        R a0 = 0;
+        R a0 = R(0);
 #pragma unroll
         for (int c = 0; c < 12; c++) {
             rv[c] = rv[c] - alpha * (res[c] + sig0 * pp[c]);
@@ -267,6 +267,13 @@ template <> struct Word<float4> {
     __device__ static void get(const float4 &w, A *o) { o[0] = w.x; o[1] = w.y; o[2] = w.z; o[3] = w.w; }
     __device__ static float4 put(const A *o) { return make_float4(o[0], o[1], o[2], o[3]); }
 };
+// float-float: one complex number per 16-byte word, (re.hi, re.lo, im.hi, im.lo)
+template <> struct Word<ffw> {
+    static constexpr int N = 2;
+    using A = ff;
+    __device__ static void get(const ffw &w, A *o) { o[0] = ff(w.rh, w.rl); o[1] = ff(w.ih, w.il); }
+    __device__ static ffw put(const A *o) { return ffw{o[0].hi, o[0].lo, o[1].hi, o[1].lo}; }
+};
 
 // y += sum_l w_l a^l p_l ; p_l = zeta_l r + b^l p_l   (words of ST; nw words per vector).
 // The active shifts are compacted into a list in shared memory and processed four at
@@ -313,8 +320,8 @@ __global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__re
                 const A wl = sw[a0 + u], bl = sb[a0 + u];
 #pragma unroll
                 for (int e = 0; e < N; e++) {
-                    yv[e] += wl * pv[e];
-                    pv[e] = rv[e] + bl * pv[e];
+                    yv[e] = fma_r(wl, pv[e], yv[e]);
+                    pv[e] = fma_r(bl, pv[e], rv[e]);
                 }
                 P[(long)sidx[a0 + u] * stride + k] = Word<ST>::put(pv);
             }
@@ -349,13 +356,14 @@ template <typename ST>
 __global__ void k_ms_init(MsState *s, const ST *__restrict__ b, ST *r, ST *y, ST *P, long stride, long nw,
                           int n, RedScratch rs) {
     constexpr int N = Word<ST>::N;
-    typename Word<ST>::A v[1] = {0};
+    using A = typename Word<ST>::A;
+    A v[1] = {A(0)};
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (long)gridDim.x * blockDim.x) {
         const ST w = b[k];
         r[k] = w;
         y[k] = w;
         for (int l = 0; l < n; l++) P[l * stride + k] = w;
-        typename Word<ST>::A e[N], a = 0;
+        A e[N], a = A(0);
         Word<ST>::get(w, e);
 #pragma unroll
         for (int q = 0; q < N; q++) a += e[q] * e[q];
@@ -498,6 +506,30 @@ cudaError_t ms_iter_f64(const Geom &g, const double2 *U, double m0, MsState *s, 
 cudaError_t ms_iter_f32(const Geom &g, const float4 *U, float m0, MsState *s, MsVectors<float4> v,
                         RedScratch rs, cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
     return ms_iter_t<float, float4, float4>(g, U, m0, s, v, rs, st, ev, ev_flags);
+}
+
+// float-float multishift: the same three kernels on float-float vectors and links (one
+// thread per site); the scalar recurrences stay FP64 on the device.
+cudaError_t ms_init_ff(const Geom &g, int n, MsState *s, MsVectors<ffw> v, const ffw *b, RedScratch rs,
+                       cudaStream_t st) {
+    k_ms_init<ffw><<<red_grid(v.stride), kBlock, 0, st>>>(s, b, v.r, v.y, v.p, v.stride, v.stride, n, rs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t ms_iter_ff(const Geom &g, const ffw *U, double m0, MsState *s, MsVectors<ffw> v, RedScratch rs,
+                       cudaStream_t st, cudaEvent_t *ev, unsigned ev_flags) {
+    const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<ff>::value, kMaxRedBlocks);
+    const ff m4(m0 + 4.0);
+    cudaError_t e;
+    if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
+    k_ms_q<ff, ffw, ffw><<<ls.grid, ls.block, 0, st>>>(g, U, m4, s, v.p, v.t, rs, ls.spb);
+    if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
+    k_ms_r<ff, ffw, ffw><<<ls.grid, ls.block, 0, st>>>(g, U, m4, s, v.t, v.p, v.r, rs, ls.spb);
+    if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
+    k_ms_shifts<ffw><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.y, v.p, v.stride, v.stride, rs.counter);
+    if (ev && (e = cudaEventRecordWithFlags(ev[3], st, ev_flags)) != cudaSuccess) return e;
+    count_launches(3);
+    return cudaGetLastError();
 }
 
 }  // namespace ovl

@@ -61,13 +61,15 @@ ovl_status fail(ovl_status s, const std::string &msg) {
     return s;
 }
 
-bool device_ptr(const void *p) {
+// Device memory of device dev (or managed memory): a pointer into another GPU's memory is
+// refused, since the kernels run on the current device.
+bool device_ptr(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
 }
 
 }  // namespace
@@ -90,15 +92,17 @@ extern "C" ovl_status wilson_apply_noalloc(double *out, const double *in, const 
         return fail(OVL_EINVAL, "wilson_apply_noalloc: lattice of " + std::to_string(V) +
                                     " sites exceeds the fixed working memory of " +
                                     std::to_string(kNoAllocMaxSites) + " sites");
-    if (!device_ptr(out) || !device_ptr(in) || !device_ptr(gauge))
-        return fail(OVL_EINVAL, "wilson_apply_noalloc: out, in and gauge must be device memory");
-    // Address of the working memory on the current device, looked up once per device.
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return fail(OVL_ECUDA, "wilson_apply_noalloc: no usable current device");
     }
+    if (!device_ptr(out, dev) || !device_ptr(in, dev) || !device_ptr(gauge, dev))
+        return fail(OVL_EINVAL, "wilson_apply_noalloc: out, in and gauge must be memory of the current device");
+    // Address of the working memory on the current device, looked up once per device and
+    // kept for the life of the process (the primary context of that device; a
+    // cudaDeviceReset or another driver context makes it stale, see include/ovl.h).
     unsigned char *scratch;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -130,6 +134,7 @@ extern "C" ovl_status wilson_apply_noalloc(double *out, const double *in, const 
     double2 *pin = (double2 *)(scratch + kNoAllocLinkBytes);
     double2 *pout = (double2 *)(scratch + kNoAllocLinkBytes + kNoAllocSpinorBytes);
     k_noalloc_pack_links<<<plain_grid(V * 4), kBlock, 0, st>>>(g, (const double2 *)gauge);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = pack_spinor_f64(g, pin, in, st)) != cudaSuccess ||
         (e = wilson_f64(g, links, pin, pout, m0, 0, 1.0, nullptr, 0.0, st)) != cudaSuccess ||

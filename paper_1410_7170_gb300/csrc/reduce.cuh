@@ -61,6 +61,32 @@ __device__ __forceinline__ void block_sum(const float vf[NV], double v[NV]) {
         warp_sum<NV>(v);
     }
 }
+// Block-wide sum of per-thread float-float values: the warp stage in float-float (both
+// words shuffled), the sum over warps in FP64 by the first warp.
+template <int NV>
+__device__ __forceinline__ void block_sum(const ff vf[NV], double v[NV]) {
+    __shared__ double sm[NV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    ff t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        t[k] = vf[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            t[k] += ff(__shfl_down_sync(0xffffffffu, t[k].hi, off), __shfl_down_sync(0xffffffffu, t[k].lo, off));
+    }
+    __syncthreads();   // protect sm from a previous use in the same kernel
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) sm[k][warp] = t[k].to_double();
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) v[k] = lane < nw ? sm[k][lane] : 0.0;
+        warp_sum<NV>(v);
+    }
+}
 template <int NV>
 __device__ __forceinline__ void block_sum(const double vd[NV], double v[NV]) {
 #pragma unroll

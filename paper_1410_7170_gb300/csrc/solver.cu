@@ -333,7 +333,7 @@ static ovl_status inner_solve(Ctx *c, const float *in, float *out) {
     return OVL_OK;
 }
 
-static ovl_status ensure_f32_buffers(Ctx *c) {
+ovl_status ensure_f32_buffers(Ctx *c) {
     if (!c->f_a) {
         void *buf;
         ST(c->alloc(&buf, (size_t)c->n64 * sizeof(float) * 2));
@@ -402,9 +402,22 @@ static double low_sign_floor(int precision) {
 }
 
 
+// The wall-clock limit of a solve (params.max_seconds), armed for the duration of one call.
+struct DeadlineScope {
+    Ctx *c;
+    DeadlineScope(Ctx *c_, std::chrono::steady_clock::time_point t0) : c(c_) {
+        c->has_deadline = c->p.max_seconds > 0;
+        if (c->has_deadline)
+            c->deadline = t0 + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                   std::chrono::duration<double>(c->p.max_seconds));
+    }
+    ~DeadlineScope() { c->has_deadline = false; }
+};
+
 ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats) {
     const auto t0 = std::chrono::steady_clock::now();
-    c->stat_ms64 = c->stat_ms32 = c->stat_prec = 0;
+    DeadlineScope dl(c, t0);
+    c->stat_ms64 = c->stat_ms32 = c->stat_msff = c->stat_prec = 0;
     c->stat_inner = 0;
     c->t_sign64 = c->t_sign_low = c->t_prec = 0;
     const bool flexible = c->p.precond != OVL_PREC_NONE;
@@ -469,7 +482,7 @@ ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, 
                 CK(spinor_f2d(c->g, (const float4 *)c->f_b, (double2 *)o, c->stream));
                 return OVL_OK;
             }
-            return c->sign64((const double2 *)a, (double2 *)o, t, 1);
+            return c->sign_outer((const double2 *)a, (double2 *)o, t, 1);
         };
         auto pc = [&](const double *a, double *o) -> ovl_status { return outer_precond(c, a, o); };
         KrylovResult kr;
@@ -492,6 +505,7 @@ ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, 
         stats->inner_iters = c->stat_inner;
         stats->ms_iters_fp64 = c->stat_ms64;
         stats->ms_iters_low = c->stat_ms32;
+        stats->ms_iters_ff = c->stat_msff;
         stats->prec_iters = c->stat_prec;
         stats->true_rel_resid = worst;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -516,8 +530,6 @@ ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, 
 // A system that has converged is dropped from the Gram-Schmidt work and its operator
 // applications are skipped inside the batched calls (tolerance <= 0).
 // ====================================================================================
-namespace {
-
 // nb FP64 <-> FP32 internal spinors back to back
 cudaError_t spinor_d2f_n(Ctx *c, const double2 *a, float4 *b, int nb) {
     for (int y = 0; y < nb; y++) {
@@ -533,6 +545,9 @@ cudaError_t spinor_f2d_n(Ctx *c, const float4 *a, double2 *b, int nb) {
     }
     return cudaSuccess;
 }
+
+namespace {
+
 // Zero the input rows of systems that are not iterating, so a nested batched solve
 // treats them as converged (zero right-hand side) and spends no work on them.
 template <typename T>
@@ -884,7 +899,7 @@ ovl_status solve_batch(Ctx *c, double2 *x, const double2 *b, int nb, double tol,
             CK(spinor_f2d_n(c, (const float4 *)fb, (double2 *)o, nb));
             return OVL_OK;
         }
-        return c->sign64_batch((const double2 *)a, (double2 *)o, nb, t, 1);
+        return c->sign_outer_batch((const double2 *)a, (double2 *)o, nb, t, 1);
     };
     auto pc = [&](const double *a, double *o, const char *act) -> ovl_status {
         if (!mixed && c->p.precond == OVL_PREC_WILSON) {

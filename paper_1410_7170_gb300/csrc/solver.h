@@ -82,6 +82,7 @@ struct Ctx {
     // gauge field (12-real links)
     double2 *U64 = nullptr;
     float4 *U32 = nullptr;
+    ffw *Uff = nullptr;           // float-float copy of U64 (made on first use)
     // boundary staging
     double *io_lex = nullptr;
     double2 *io_a = nullptr, *io_b = nullptr;
@@ -99,7 +100,9 @@ struct Ctx {
     MsVectors<float4> ms32{};
     MsVectorsH msh{};
     MsState *msh_state = nullptr;
-    GraphSlot graphs[6];
+    MsVectors<ffw> msff{};             // float-float multishift vectors
+    MsState *msff_state = nullptr;
+    GraphSlot graphs[8];
     // batched multishift (several right-hand sides in lock-step)
     MsBatch<double2> msb64{};
     MsBatch<float4> msb32{};
@@ -112,10 +115,10 @@ struct Ctx {
     void *h_pinned_b = nullptr;
     // instrumentation
     bool prof = false;
-    ProfAcc pacc[2];   // per precision slot (0 FP64, 1 FP32)
+    ProfAcc pacc[3];   // per arithmetic slot (0 FP64, 1 FP32 / 16-bit stored, 2 float-float)
     long launch_mark = 0;
-    cudaEvent_t ev[2][4] = {};   // profiling: events around the kernels of one sampled iteration
-    bool ev_ready[2] = {false, false};
+    cudaEvent_t ev[3][4] = {};   // profiling: events around the kernels of one sampled iteration
+    bool ev_ready[3] = {false, false, false};
     int *d_hist = nullptr;
     int hist_cap = 0;
     int *h_hist = nullptr;
@@ -133,7 +136,7 @@ struct Ctx {
     void *sap_r32 = nullptr, *sap_r64 = nullptr;   // SAP residual scratch
     double2 *d_x = nullptr, *d_b = nullptr; // FP64 solve vectors
     // statistics of the running call
-    long stat_ms64 = 0, stat_ms32 = 0, stat_prec = 0;
+    long stat_ms64 = 0, stat_ms32 = 0, stat_msff = 0, stat_prec = 0;
     int stat_inner = 0;
     float tune_ms[4] = {0, 0, 0, 0};   // stencil ms: fp64 1/4 tps, fp32 1/4 tps
     int sap_tps = 1;                   // threads per site of the FP32 Schwarz block kernel
@@ -154,6 +157,15 @@ struct Ctx {
     double2 *ks_f = nullptr, *ks_tmp = nullptr;       // accumulated f(Q^2) Q b, stencil scratch
     double *ks_S = nullptr;                           // Ritz coefficients (device)
     long ks_cycles = 0, ks_matvecs = 0;               // totals since creation
+    // wall-clock limit of the running ovl_solve (params.max_seconds; 0 = none)
+    std::chrono::steady_clock::time_point deadline{};
+    bool has_deadline = false;
+    // true (with err set) once the running solve is past its wall-clock limit
+    bool past_deadline() {
+        if (!has_deadline || std::chrono::steady_clock::now() < deadline) return false;
+        err = "ovl_solve: wall-clock limit params.max_seconds reached";
+        return true;
+    }
 
     ~Ctx();
     ovl_status alloc(void **p, size_t bytes);
@@ -171,7 +183,15 @@ struct Ctx {
     template <typename Iter>
     ovl_status ms_run(MsState *d_state, int which, int slot, double shift_bytes, Iter iter_fn, int *iters_out);
     ovl_status sign64(const double2 *b, double2 *out, double tol, int mode);
-    ovl_status sign32(const float4 *b, float4 *out, double tol, int mode);
+    // store: -1 = from params.precision, 0 = FP32, 1 = FP16-stored, 2 = BF16-stored directions
+    ovl_status sign32(const float4 *b, float4 *out, double tol, int mode, int store = -1);
+    // the FP64-accuracy sign in float-float arithmetic on FP64 even-odd vectors b, out
+    ovl_status sign_ff(const double2 *b, double2 *out, double tol, int mode);
+    ovl_status ensure_ff_links();
+    ovl_status ensure_msff();
+    // FP64-accuracy sign of the outer solver: float-float in the mixed precisions when
+    // params.ff_outer is set, native FP64 otherwise
+    ovl_status sign_outer(const double2 *b, double2 *out, double tol, int mode);
     ovl_status sign64_krylov(const double2 *b, double2 *out, double tol, int mode);
     ovl_status ensure_ksign();
     ovl_status ensure_ms64();
@@ -180,6 +200,7 @@ struct Ctx {
     // several right-hand sides: b, out hold nrhs internal vectors back to back
     ovl_status ensure_batch();
     ovl_status sign64_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode);
+    ovl_status sign_outer_batch(const double2 *b, double2 *out, int nrhs, const double *tol, int mode);
     ovl_status sign32_batch(const float4 *b, float4 *out, int nrhs, const double *tol, int mode);
     template <typename ST, typename Init, typename Iter>
     ovl_status msb_run(int nrhs, const double *tol, int n, int slot, Init init_fn, Iter iter_fn, long *iters_out);
@@ -213,6 +234,11 @@ struct PhaseClock {
 ovl_status upload_coef(Ctx *c, const std::vector<std::complex<double>> &v);
 
 ovl_status solve_all(Ctx *c, double *x, const double *b, int n_rhs, double tol, ovl_stats *stats);
+// FP32 conversion buffers f_a, f_b (one spinor each), allocated on first use
+ovl_status ensure_f32_buffers(Ctx *c);
+// FP64 <-> FP32 even-odd conversion of nb spinors back to back
+cudaError_t spinor_d2f_n(Ctx *c, const double2 *a, float4 *b, int nb);
+cudaError_t spinor_f2d_n(Ctx *c, const float4 *a, double2 *b, int nb);
 // Lock-step batched solve of nrhs <= kMaxBatch systems on internal FP64 vectors.
 ovl_status solve_batch(Ctx *c, double2 *x, const double2 *b, int nrhs, double tol, int *outer_iters,
                        double *worst_res, bool *all_conv);

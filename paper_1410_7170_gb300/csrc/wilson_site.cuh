@@ -15,6 +15,7 @@
 // a sign-bit flip of the projected half spinor.
 #pragma once
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace ovl {
 
@@ -24,6 +25,8 @@ template <>
 __device__ __forceinline__ double fma_r<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <>
 __device__ __forceinline__ float fma_r<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ ff fma_r<ff>(ff a, ff b, ff c) { return ff_fma(a, b, c); }
 
 // o = u h and o = u^H h as explicit chains of fused multiply-adds: per output real one
 // multiply and five FMAs. Summing separately rounded complex products would cost two
@@ -71,6 +74,7 @@ __device__ __forceinline__ double flip_sign(double x, bool neg) {
 __device__ __forceinline__ float flip_sign(float x, bool neg) {
     return __int_as_float(__float_as_int(x) ^ (neg ? (int)0x80000000u : 0));
 }
+__device__ __forceinline__ ff flip_sign(ff x, bool neg) { return ff(flip_sign(x.hi, neg), flip_sign(x.lo, neg)); }
 template <typename R>
 __device__ __forceinline__ void flip_half(cpx<R> h0[3], cpx<R> h1[3], bool neg) {
 #pragma unroll

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import sparse
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -40,19 +41,30 @@ def test_noalloc_matches_wilson_apply_on_consecutive_calls(dims, ap, m0):
     for x, o in zip(ins, outs):                 # two calls in a row on the same stream
         ovl.wilson_apply_noalloc(o, x, U, dims, m0, antiperiodic=ap)
     torch.cuda.synchronize()
-    for o, r in zip(outs, refs):
+    for x, o, r in zip(ins, outs, refs):
         assert torch.isfinite(o).all()
         err = ((o - r).abs().max() / r.abs().max()).item()
         assert err < 1e-13
+        # and against the oracle's definitional stencil directly
+        ref = sparse.wilson(x.cpu().numpy(), U.cpu().numpy(), dims, m0, antiperiodic=ap)
+        oh = o.cpu().numpy()
+        assert np.abs(oh - ref).max() < 1e-13 * np.abs(ref).max()
 
 
 def test_noalloc_rejects_what_does_not_fit():
     dims = (16, 16, 16, 16)                      # 65536 sites > the fixed working memory
-    U = torch.zeros((2, 4, 3, 3), dtype=torch.complex128, device="cuda")
-    x = torch.zeros((2, 4, 3), dtype=torch.complex128, device="cuda")
+    V = 16 ** 4
+    U = torch.zeros((V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    x = torch.zeros((V, 4, 3), dtype=torch.complex128, device="cuda")
     with pytest.raises(ovl.OvlError) as e:
         ovl.wilson_apply_noalloc(x, x, U, dims, -1.0)
     assert e.value.status == ovl.OVL_EINVAL and "16384" in str(e.value)
+    # buffers smaller than the lattice, or of another dtype, are refused before the call
+    small = (4, 4, 4, 4)
+    with pytest.raises(ValueError):
+        ovl.wilson_apply_noalloc(x[:10], x[:256], U[:256], small, -1.0)
+    with pytest.raises(ValueError):
+        ovl.wilson_apply_noalloc(x[:256].to(torch.complex64), x[:256], U[:256], small, -1.0)
     small = (4, 4, 4, 4)
     Uh = synth.gauge_field(small, 0.3, 1)
     xh = synth.rhs_gaussian(small, 2)
