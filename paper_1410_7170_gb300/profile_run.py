@@ -1,7 +1,7 @@
 """Runs one operation of a workload through the library's public API, for external
 profilers (ncu). Nothing is timed here; the benchmark is bench.py.
 
-    python -m paper_1410_7170_gb300.profile_run --what solve_mixed|solve_fp64|sign64|sign64_krylov|sap|dslash64|dslash32
+    python -m paper_1410_7170_gb300.profile_run --what solve_mixed|solve_fp64|sign64|sign_ff|sign64_krylov|sap|dslash64|dslash32|dslash_ff
         [--lattice 16x16x16x16] [--stout 3] [--stencil-tps 1] [--sap-tps 1]
 
 The gauge field, right-hand side and solver settings are those of bench.py's 16^4
@@ -27,7 +27,8 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--what", required=True,
-                    choices=["solve_mixed", "solve_fp64", "sign64", "sign64_krylov", "sap", "dslash64", "dslash32"])
+                    choices=["solve_mixed", "solve_fp64", "sign64", "sign_ff", "sign64_krylov", "sap", "dslash64",
+                             "dslash32", "dslash_ff"])
     ap.add_argument("--lattice", default="16x16x16x16")
     ap.add_argument("--stout", type=int, default=3)
     ap.add_argument("--stencil-tps", type=int, default=0)
@@ -55,10 +56,12 @@ def main():
         print(stats)
     elif a.what in ("sign64", "sign64_krylov"):
         op.sign_apply(x, b, 1e-8)
+    elif a.what == "sign_ff":
+        op.sign_apply_arith(x, b, 1e-8, ovl.OVL_ARITH_FF)
     elif a.what == "sap":
         op.sap_apply(x, b, -0.266)   # m0^def of the 16^4 workload field (Eq. default_m)
     else:
-        print(op.dslash_time(0 if a.what == "dslash64" else 1, 3), "ms")
+        print(op.dslash_time({"dslash64": 0, "dslash32": 1, "dslash_ff": 2}[a.what], 3), "ms")
     torch.cuda.synchronize()
     op.close()
 
