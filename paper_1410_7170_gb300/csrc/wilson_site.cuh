@@ -14,6 +14,8 @@
 // Antiperiodic time boundary: hops across the x0 boundary carry a factor -1, applied as
 // a sign-bit flip of the projected half spinor.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "ff.cuh"
 
@@ -67,6 +69,83 @@ __device__ __forceinline__ void su3_dag_mul(const cpx<R> u[3][3], const cpx<R> h
     }
 }
 
+// Float-float SU(3) x vector: each output real is a sum of six products, accumulated as one
+// running FP32 sum of the leading products (TwoSum keeps it exact) and one FP32 word that
+// collects every rounding error and cross term, renormalised once at the end: 12 FP32
+// instructions per product against 15 for a renormalised float-float FMA, and a shorter
+// instruction stream (the float-float stencil is large enough to miss the instruction cache).
+struct ff_dot {
+    float s, e;
+    __device__ __forceinline__ void first(ff a, ff b) {
+        s = __fmul_rn(a.hi, b.hi);
+        e = __fmaf_rn(a.hi, b.hi, -s);
+        e = __fmaf_rn(a.hi, b.lo, e);
+        e = __fmaf_rn(a.lo, b.hi, e);
+    }
+    __device__ __forceinline__ void add(ff a, ff b) {
+        const float p = __fmul_rn(a.hi, b.hi);
+        const float ep = __fmaf_rn(a.hi, b.hi, -p);
+        const ff t = ff_two_sum(s, p);
+        s = t.hi;
+        e = __fadd_rn(e, __fadd_rn(t.lo, ep));
+        e = __fmaf_rn(a.hi, b.lo, e);
+        e = __fmaf_rn(a.lo, b.hi, e);
+    }
+    __device__ __forceinline__ ff done() const { return ff_fast_two_sum(s, e); }
+};
+template <>
+__device__ __forceinline__ void su3_mul<ff>(const cpx<ff> u[3][3], const cpx<ff> h[3], cpx<ff> o[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        ff_dot re, im;
+        re.first(u[a][0].re, h[0].re);
+        im.first(u[a][0].re, h[0].im);
+        re.add(-u[a][0].im, h[0].im);
+        im.add(u[a][0].im, h[0].re);
+#pragma unroll
+        for (int b = 1; b < 3; b++) {
+            re.add(u[a][b].re, h[b].re);
+            im.add(u[a][b].re, h[b].im);
+            re.add(-u[a][b].im, h[b].im);
+            im.add(u[a][b].im, h[b].re);
+        }
+        o[a] = cpx<ff>{re.done(), im.done()};
+    }
+}
+template <>
+__device__ __forceinline__ void su3_dag_mul<ff>(const cpx<ff> u[3][3], const cpx<ff> h[3], cpx<ff> o[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        ff_dot re, im;
+        re.first(u[0][a].re, h[0].re);
+        im.first(u[0][a].re, h[0].im);
+        re.add(u[0][a].im, h[0].im);
+        im.add(-u[0][a].im, h[0].re);
+#pragma unroll
+        for (int b = 1; b < 3; b++) {
+            re.add(u[b][a].re, h[b].re);
+            im.add(u[b][a].re, h[b].im);
+            re.add(u[b][a].im, h[b].im);
+            im.add(-u[b][a].im, h[b].re);
+        }
+        o[a] = cpx<ff>{re.done(), im.done()};
+    }
+}
+
+// Accumulation of hop contributions: a + b, except in float-float, where the hop
+// accumulator is summed without renormalising (TwoSum of the leading words, FP32 sum of the
+// rest: 8 instructions instead of 11); wilson_combine renormalises the result.
+template <typename R>
+__device__ __forceinline__ cpx<R> cadd_acc(cpx<R> a, cpx<R> b) { return a + b; }
+__device__ __forceinline__ ff ff_add_lazy(ff a, ff b) {
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+template <>
+__device__ __forceinline__ cpx<ff> cadd_acc<ff>(cpx<ff> a, cpx<ff> b) {
+    return cpx<ff>{ff_add_lazy(a.re, b.re), ff_add_lazy(a.im, b.im)};
+}
+
 // -x where neg != 0, by flipping the sign bit (integer pipe, exact)
 __device__ __forceinline__ double flip_sign(double x, bool neg) {
     return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
@@ -116,10 +195,10 @@ __device__ __forceinline__ void acc_fwd(int mu, cpx<R> acc[12], const cpx<R> a0[
             acc[6 + c] = l2;
             acc[9 + c] = l3;
         } else {
-            acc[c] = acc[c] + a0[c];
-            acc[3 + c] = acc[3 + c] + a1[c];
-            acc[6 + c] = acc[6 + c] + l2;
-            acc[9 + c] = acc[9 + c] + l3;
+            acc[c] = cadd_acc(acc[c], a0[c]);
+            acc[3 + c] = cadd_acc(acc[3 + c], a1[c]);
+            acc[6 + c] = cadd_acc(acc[6 + c], l2);
+            acc[9 + c] = cadd_acc(acc[9 + c], l3);
         }
     }
 }
@@ -142,13 +221,13 @@ template <typename R>
 __device__ __forceinline__ void acc_bwd(int mu, cpx<R> acc[12], const cpx<R> a0[3], const cpx<R> a1[3]) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        acc[c] = acc[c] + a0[c];
-        acc[3 + c] = acc[3 + c] + a1[c];
+        acc[c] = cadd_acc(acc[c], a0[c]);
+        acc[3 + c] = cadd_acc(acc[3 + c], a1[c]);
         switch (mu) {
-            case 0: acc[6 + c] = acc[6 + c] + a0[c];        acc[9 + c] = acc[9 + c] + a1[c];        break;
-            case 1: acc[6 + c] = acc[6 + c] + mul_i(a1[c]); acc[9 + c] = acc[9 + c] + mul_i(a0[c]); break;
-            case 2: acc[6 + c] = acc[6 + c] + a1[c];        acc[9 + c] = acc[9 + c] - a0[c];        break;
-            default: acc[6 + c] = acc[6 + c] + mul_i(a0[c]); acc[9 + c] = acc[9 + c] + mul_mi(a1[c]); break;
+            case 0: acc[6 + c] = cadd_acc(acc[6 + c], a0[c]);        acc[9 + c] = cadd_acc(acc[9 + c], a1[c]);        break;
+            case 1: acc[6 + c] = cadd_acc(acc[6 + c], mul_i(a1[c])); acc[9 + c] = cadd_acc(acc[9 + c], mul_i(a0[c])); break;
+            case 2: acc[6 + c] = cadd_acc(acc[6 + c], a1[c]);        acc[9 + c] = cadd_acc(acc[9 + c], -a0[c]);       break;
+            default: acc[6 + c] = cadd_acc(acc[6 + c], mul_i(a0[c])); acc[9 + c] = cadd_acc(acc[9 + c], mul_mi(a1[c])); break;
         }
     }
 }
@@ -184,6 +263,46 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const LT *__restrict__ U,
         su3_dag_mul(u, h0, a0);
         su3_dag_mul(u, h1, a1);
         acc_bwd(MU, acc, a0, a1);
+    }
+}
+
+// The two hops of direction mu (a run-time value) at site (p, i), added into acc. The
+// float-float stencil loops over mu with this body instead of unrolling four copies: its
+// fully unrolled form runs to more than 12k instructions per site and stalls on instruction
+// fetch. Neighbour coordinates are formed with selects, not by indexing x with mu (that
+// would put x in local memory).
+template <typename R, typename LT, typename ST>
+__device__ __forceinline__ void hop_dir_rt(const Geom &g, const LT *__restrict__ U, ST in, int p, int i, const int x[4],
+                                           int mu, cpx<R> acc[12]) {
+    const int q = 1 - p;
+    int yf[4], yb[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const bool on = m == mu;
+        yf[m] = on ? (x[m] + 1 == g.L[m] ? 0 : x[m] + 1) : x[m];
+        yb[m] = on ? (x[m] == 0 ? g.L[m] - 1 : x[m] - 1) : x[m];
+    }
+    {   // forward neighbour x + mu, link U_mu(x) stored at (p, i)
+        const int j = eo_index(g, yf);
+        cpx<R> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
+        load_spinor<R>(in, g.Vh, q, j, s);
+        load_link<R>(U, g.Vh, p, mu, i, u);
+        proj_fwd(mu, s, h0, h1);
+        flip_half(h0, h1, mu == 0 && g.antiperiodic && x[0] == g.L[0] - 1);
+        su3_mul(u, h0, a0);
+        su3_mul(u, h1, a1);
+        acc_fwd<false>(mu, acc, a0, a1);
+    }
+    {   // backward neighbour x - mu, link U_mu(x - mu)^H stored at (q, j)
+        const int j = eo_index(g, yb);
+        cpx<R> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
+        load_spinor<R>(in, g.Vh, q, j, s);
+        load_link<R>(U, g.Vh, q, mu, j, u);
+        proj_bwd(mu, s, h0, h1);
+        flip_half(h0, h1, mu == 0 && g.antiperiodic && x[0] == 0);
+        su3_dag_mul(u, h0, a0);
+        su3_dag_mul(u, h1, a1);
+        acc_bwd(mu, acc, a0, a1);
     }
 }
 
@@ -251,10 +370,17 @@ __device__ __forceinline__ void wilson_hop(const Geom &g, const LT *__restrict__
                                            cpx<R> acc[12]) {
     int x[4];
     eo_coords(g, p, i, x);
-    hop_dir<0, true, R>(g, U, in, p, i, x, acc);
-    hop_dir<1, false, R>(g, U, in, p, i, x, acc);
-    hop_dir<2, false, R>(g, U, in, p, i, x, acc);
-    hop_dir<3, false, R>(g, U, in, p, i, x, acc);
+    if constexpr (std::is_same<R, ff>::value) {
+#pragma unroll
+        for (int c = 0; c < 12; c++) acc[c] = cpx<R>{R(0), R(0)};
+#pragma unroll 1
+        for (int mu = 0; mu < 4; mu++) hop_dir_rt<R>(g, U, in, p, i, x, mu, acc);
+    } else {
+        hop_dir<0, true, R>(g, U, in, p, i, x, acc);
+        hop_dir<1, false, R>(g, U, in, p, i, x, acc);
+        hop_dir<2, false, R>(g, U, in, p, i, x, acc);
+        hop_dir<3, false, R>(g, U, in, p, i, x, acc);
+    }
 }
 
 // res = (m0+4) own + hop, where hop (formed with the stored links -1/2 U) is -1/2 times the
