@@ -39,8 +39,8 @@ PROF_CLASSES = ("ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_
 # relaxation), the oracle's own algorithm: D_N applications per solve, measured with the
 # library (ovl_solve, precond none, relax 0) and spectral interval of |Q| from its Lanczos
 # estimate; used to project the oracle's measured sign time to solves/s.
-ORACLE_DN_PER_SOLVE = 120
-ORACLE_INTERVAL = (0.2446, 7.2368)
+ORACLE_DN_PER_SOLVE = 118        # 117 GMRES iterations + the final true residual (GB300 run)
+ORACLE_INTERVAL = (0.5096977520013128, 7.211298398975124)
 
 
 def kernel_hash():
@@ -320,7 +320,7 @@ def run_ours(args, rank, world, dist):
                     for k, v in kern.items() if v["launches"]},
         "peaks_measured": {"fp64_fma_gflops": round(fp64_fma, 1), "fp32_fma_gflops": round(fp32_fma, 1),
                            "hbm_gbs": pk["hbm_gbs"]},
-        "mixed_stats": {k: (round(v, 6) if isinstance(v, float) else v) for k, v in st_mixed[-1].items()},
+        "mixed_stats": {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in st_mixed[-1].items()},
         "tuning": {"stencil_tps_fp64": tuning["tps64"], "stencil_tps_fp32": tuning["tps32"],
                    "sap_tps": tuning_sap["sap_tps"]},
     }
@@ -335,7 +335,52 @@ def run_ours(args, rank, world, dist):
                        "library_true_rel_resid": st_mixed[-1]["true_rel_resid"],
                        "oracle_rel_resid": acc, "oracle_check": acc_cost, "solution_err_vs_1e-12_solve": sol_err,
                        "ref_solve_true_rel_resid": st_ref["true_rel_resid"]}
-    return out
+    if args.details:
+        with open(args.details, "w") as f:
+            json.dump(out, f, indent=1)
+    return compact_line(out)
+
+
+def compact_line(out):
+    """The one JSON line: the contract's keys, then short summaries of the other sections, with
+    the metric's own comparisons (mixed vs FP64 GPU) and the accuracy of the headline result
+    last. The full record goes to --details."""
+    keep = ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "clocks", "cpu_baseline"]
+    line = {k: out[k] for k in keep}
+    r = out["roofline"]
+    line["roofline"] = {k: r[k] for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "peak_kind",
+                                          "traffic", "avg_launch_us", "launches")}
+    line["kernels"] = {k: [v["share"], v["avg_us"]] for k, v in out["kernels"].items()}
+    line["peaks_measured"] = out["peaks_measured"]
+    d = out["dslash"]
+    line["dslash_64x32x32x32"] = {
+        "fp32_GBps": round(d["fp32"]["GB/s"], 1), "fp32_frac_hbm": round(d["fp32"]["frac_hbm"], 4),
+        "float_float_ms": round(d["float_float"]["ms"], 4), "fp64_ms": round(d["fp64"]["ms"], 4),
+        "fp32_ms_per_rhs_1_4_12": [round(d["fp32"]["ms"], 4), round(d["fp32_rhs4"]["ms_per_rhs"], 4),
+                                   round(d["fp32_rhs12"]["ms_per_rhs"], 4)]}
+    sm = out["sign_methods"]
+    line["sign_ms_16x16x16x16_tol1e-10"] = {"fp64_multishift": round(sm["zolotarev_multishift"]["ms"], 2),
+                                            "float_float_multishift": round(sm["float_float_multishift"]["ms"], 2),
+                                            "fp64_krylov_thick_restart": round(sm["krylov_thick_restart"]["ms"], 2)}
+    sv = out["serving"]
+    line["serving"] = {k: sv[k] for k in ("p50_s", "p99_s", "solves_per_s", "completed", "failed")}
+    line["mixed_stats"] = {k: out["mixed_stats"][k] for k in ("outer_iters", "inner_iters", "ms_iters_ff",
+                                                               "ms_iters_low", "prec_iters")}
+    for k in ("fp64_gpu", "mixed_over_fp64", "accuracy"):
+        line[k] = out[k]
+    return {k: (v if k in ("value", "ms_per_step") else _sig(v)) for k, v in line.items()}
+
+
+def _sig(v, digits=5):
+    """Floats rounded to `digits` significant digits, recursively (keeps the line short)."""
+    if isinstance(v, float):
+        return float("%.*g" % (digits, v))
+    if isinstance(v, dict):
+        return {k: _sig(x, digits) for k, x in v.items()}
+    if isinstance(v, list):
+        return [_sig(x, digits) for x in v]
+    return v
 
 
 def oracle_check(U, b, x, info, tol=1e-10):
@@ -548,6 +593,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--details", default="", help="also write the full record (every section) to this JSON file")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

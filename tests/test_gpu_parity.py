@@ -233,7 +233,9 @@ def test_deflation_cuts_multishift_work_16x16x16x16():
             d = op.deflation_info()
             assert d["lambda_next"] > op.info()["lambda_min"] and d["resid_max"] < 1e-8
         op.close()
-    assert stats[24]["ms_iters_fp64"] < stats[0]["ms_iters_fp64"], stats
+    # the FP64-accuracy sign runs in float-float in the mixed solver (ff_outer, the default)
+    tight = {k: stats[k]["ms_iters_fp64"] + stats[k]["ms_iters_ff"] for k in stats}
+    assert tight[24] < tight[0], stats
     assert stats[24]["ms_iters_low"] < stats[0]["ms_iters_low"], stats
 
 
@@ -397,25 +399,32 @@ def test_sap_threads_per_site_variants_agree(dims):
     assert max(res.values()) < 1.5e-4, res
 
 
-def test_profiling_counters_are_consistent():
+@pytest.mark.parametrize("ff_outer", [0, 1])
+def test_profiling_counters_are_consistent(ff_outer):
     """The instrumentation samples one multishift iteration per queued chunk: the timed
-    launches are a subset of all launches, with positive times and bytes."""
+    launches are a subset of all launches, with positive times and bytes. The tight sign
+    applications run in native FP64 (ff_outer = 0) or in float-float (ff_outer = 1)."""
     dims = (8, 8, 8, 8)
     U = synth.gauge_field(dims, 0.5, 1204, stout_steps=3)
     b = torch.from_numpy(synth.rhs_gaussian(dims, 2204)).cuda()
     op = ovl.Overlap(torch.from_numpy(U).cuda(), dims, 1.0, 0.01,
-                     ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32))
+                     ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32,
+                                        ff_outer=ff_outer))
     op.prof_enable(True)
     op.prof_get(reset=True)
     x = torch.zeros_like(b)
     st, stats = op.ovl_solve(x, b, 1, 1e-8)
     pr = op.prof_get(reset=True)
     assert pr["valid"] == 1 and pr["launches"] > 0
-    for name in ("ms_stencil_f64", "ms_shifts_f64", "ms_stencil_f32", "ms_shifts_f32"):
+    tight = "ff" if ff_outer else "f64"
+    idle = "f64" if ff_outer else "ff"
+    for name in ("ms_stencil_" + tight, "ms_shifts_" + tight, "ms_stencil_f32", "ms_shifts_f32"):
         k = pr[name]
         assert 0 < k["timed"] <= k["launches"], (name, k)
         assert k["ms"] > 0 and 0 < k["timed_bytes"] <= k["bytes"], (name, k)
-    assert pr["ms_stencil_f64"]["launches"] == 2 * stats["ms_iters_fp64"]
+    assert pr["ms_stencil_" + idle]["launches"] == 0 and pr["ms_shifts_" + idle]["launches"] == 0
+    n_tight = stats["ms_iters_ff"] if ff_outer else stats["ms_iters_fp64"]
+    assert pr["ms_stencil_" + tight]["launches"] == 2 * n_tight
     assert pr["ms_shifts_f32"]["launches"] == stats["ms_iters_low"]
     assert stats["t_sign_fp64"] > 0 and stats["t_sign_low"] > 0 and stats["t_prec"] > 0
     assert stats["t_sign_fp64"] + stats["t_sign_low"] + stats["t_prec"] <= stats["seconds"]
