@@ -126,6 +126,8 @@ void run_job(ovl_server *s, Job *j) {
     const size_t cbytes = j->claimed_bytes;
     ovl_status st = OVL_OK;
     if (!ctx) st = ovl_create(&ctx, j->req.gauge, j->req.dims, j->req.rho, j->req.mu, &j->params, nullptr);
+    // the admission estimate reserved the batch workspaces: batch by rhs_block alone
+    if (ctx) reinterpret_cast<ovl::Ctx *>(ctx)->fixed_batch = true;
     ovl_stats stats;
     memset(&stats, 0, sizeof(stats));
     if (st == OVL_OK) st = ovl_solve(ctx, j->req.x, j->req.b, j->req.n_rhs, j->req.tol, &stats);

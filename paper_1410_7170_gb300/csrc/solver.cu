@@ -828,6 +828,7 @@ static size_t batch_bytes_per_rhs(const Ctx *c) {
 }
 
 int batch_size_for(Ctx *c, int want) {
+    if (c->fixed_batch) return std::max(1, std::min(want, kMaxBatch));
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
         cudaGetLastError();

@@ -157,6 +157,10 @@ struct Ctx {
     double2 *ks_f = nullptr, *ks_tmp = nullptr;       // accumulated f(Q^2) Q b, stencil scratch
     double *ks_S = nullptr;                           // Ritz coefficients (device)
     long ks_cycles = 0, ks_matvecs = 0;               // totals since creation
+    // batches of several right-hand sides sized by params.rhs_block alone, not by the free
+    // device memory (set by the serving loop, which reserves that memory at admission, so
+    // that a request's batching does not depend on what else is running)
+    bool fixed_batch = false;
     // wall-clock limit of the running ovl_solve (params.max_seconds; 0 = none)
     std::chrono::steady_clock::time_point deadline{};
     bool has_deadline = false;

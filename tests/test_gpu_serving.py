@@ -67,11 +67,11 @@ def test_mixed_stream_matches_each_request_alone():
         op = ovl.Overlap(r["gauge"], r["dims"], 1.0, r["mu"], _params())
         xa = np.zeros_like(r["b"])
         op.ovl_solve(xa, r["b"], r["n_rhs"], TOL)
-        rho = (1.0 + r["mu"] / 2) / (1.0 - r["mu"] / 2)
-        kappa = (rho + 1.0) / (rho - 1.0)                    # D_N is normal, spectrum on |z - rho| = 1
         for k in range(r["n_rhs"]):
+            # the same kernels, launch shapes, batching and reduction orders run whatever else
+            # is on the GPU, so the served result is the one computed alone, bit for bit
             d = np.linalg.norm(x[k] - xa[k]) / np.linalg.norm(xa[k])
-            assert d <= 2.5 * kappa * TOL, (d, r["dims"], r["mu"])
+            assert d == 0.0, (d, r["dims"], r["mu"], r["n_rhs"])
             # and the served result solves its system
             ax = np.empty_like(x[k])
             op.ovl_apply(ax, x[k], 1e-12)
