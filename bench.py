@@ -158,12 +158,21 @@ def make_inputs(rank):
     return U, b
 
 
+# Relaxation factor of the sign accuracy eps_sign = tol / ||r_k|| * RELAX (Sec. 5.2; Table 2 uses
+# 1e-2). Measured on this workload, both arms: 0.3 needs the fewest multishift iterations at an
+# unchanged outer iteration count (mixed 149 -> 121 ms, FP64 1.26 -> 1.11 s per solve; 1.0 needs
+# more outer iterations). The solve still stops on its true residual, recomputed at full accuracy.
+RELAX = 0.3
+
+
 def solver_params(ovl, mixed):
     if mixed:
-        return ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, ff_outer=1)
+        return ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, ff_outer=1,
+                                  relax_factor=RELAX)
     # plain FP64 arm: its best preconditioner budget (4 Wilson iterations per application gave
     # the same outer iteration count as the eps_prec = 0.1 solve at half the time)
-    return ovl.params_default(precond=ovl.OVL_PREC_WILSON, precision=ovl.OVL_FP64, prec_max_iter=4)
+    return ovl.params_default(precond=ovl.OVL_PREC_WILSON, precision=ovl.OVL_FP64, prec_max_iter=4,
+                              relax_factor=RELAX)
 
 
 def run_ours(args, rank, world, dist):
@@ -302,7 +311,7 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic (seeded SU(3) links exp(i 0.5 H), 3 stout steps; Gaussian RHS)",
         "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "rho": 1.0, "mu": 0.01,
                    "tol": TOL, "solver": "FGMRES(100) fp64 + inner FGMRES fp32 (Table 3) + Wilson FGMRES fp32",
-                   "n_poles": 20, "l2": "flushed (256 MB write) before every timed step",
+                   "n_poles": 20, "relax_factor": RELAX, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": (achieved / peak) if achieved else None, "peak_kind": pkind,
@@ -357,6 +366,7 @@ def compact_line(out):
     line["dslash_64x32x32x32"] = {
         "fp32_GBps": round(d["fp32"]["GB/s"], 1), "fp32_frac_hbm": round(d["fp32"]["frac_hbm"], 4),
         "float_float_ms": round(d["float_float"]["ms"], 4), "fp64_ms": round(d["fp64"]["ms"], 4),
+        "fp16_GBps": round(d["fp16"]["GB/s"], 1), "fp16_frac_hbm": round(d["fp16"]["frac_hbm"], 4),
         "fp32_ms_per_rhs_1_4_12": [round(d["fp32"]["ms"], 4), round(d["fp32_rhs4"]["ms_per_rhs"], 4),
                                    round(d["fp32_rhs12"]["ms_per_rhs"], 4)]}
     sm = out["sign_methods"]
@@ -476,9 +486,12 @@ def dslash(ovl, torch, dev, hbm_gbs, dims=(64, 32, 32, 32)):
     U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1004, stout_steps=0, device=dev)).to(dev)
     op = ovl.Overlap(U, dims, 1.0, 0.01, ovl.params_default(lambda_min=0.3, lambda_max=7.3))
     out = {"lattice": "x".join(map(str, dims)), "byte_model": "96 reals/site (48 link + 24 in + 24 out)"}
-    for prec, name, w in ((1, "fp32", 4), (0, "fp64", 8), (2, "float_float", 8)):
+    # algorithmic bytes per site: 96 reals (FP64 and float-float 8 B, FP32 4 B); 16-bit: 4 links x
+    # 24 B + in and out spinors of 48 B (+ 4 B per-site scale in FP16)
+    for prec, name, bps in ((1, "fp32", 384), (0, "fp64", 768), (2, "float_float", 768), (3, "fp16", 200),
+                            (4, "bf16", 192)):
         ms = op.dslash_time(prec, 20)
-        gbs = 96 * V * w / (ms * 1e-3) / 1e9
+        gbs = bps * V / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "GB/s": gbs, "frac_hbm": gbs / hbm_gbs, "GFLOP/s": 1368 * V / (ms * 1e-3) / 1e9}
     for nr in (4, 12):
         ms = op.dslash_time_n(1, nr, 10)
@@ -538,6 +551,82 @@ def serving(ovl, torch, dev, n_req=24, slots=3, seed=5000):
             "completed": st["completed"], "failed": st["failed"], "hbm_high_water_bytes": st["hbm_high_water"]}
 
 
+def serving_full(seed=5000, n_req=200, slots=3, n_cap=40, n_alone=8):
+    """The full serving workload: Poisson arrivals of n_req overlap solves, lattice V uniform in
+    {8^4, 16^4, 24^4, 32^4}, mu in {0.01, 0.05, 0.1}, 1-12 Gaussian right-hand sides, each
+    request with its own gauge field (generator seeded by the request id, 3 stout steps), tol
+    1e-8. The arrival rate is 0.7 x the capacity measured first on the first n_cap requests
+    submitted at once. Reported: p50/p99 latency, solves/s, HBM high-water mark, the worst true
+    residual, and the largest difference between a served result and the same request run
+    alone (n_alone requests re-run alone)."""
+    import numpy as np
+    import torch
+
+    import paper_1410_7170_gb300 as ovl
+    from paper_1410_7170_gb300 import build
+    import synth
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(seed)
+    sizes = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 32)]
+    reqs = []
+    for k in range(n_req):
+        d = sizes[int(rng.integers(4))]
+        reqs.append(dict(id=k, dims=d, mu=float(rng.choice([0.01, 0.05, 0.1])), n_rhs=int(rng.integers(1, 13))))
+    # inputs resident on the device before the stream starts: one gauge field per request, and
+    # per lattice size one block of 12 Gaussian right-hand sides that requests read from
+    for r in reqs:
+        r["gauge"] = torch.from_numpy(synth.gauge_field(r["dims"], 0.5, seed + r["id"], stout_steps=3,
+                                                        device=dev)).to(dev)
+    bblk = {d: torch.from_numpy(synth.rhs_gaussian(d, seed + 1000 + i, n_rhs=12)).to(dev)
+            for i, d in enumerate(sizes)}
+    p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, relax_factor=RELAX)
+
+    def run(sub, rate):
+        srv = ovl.Server(slots=slots)
+        xs, tk = [], []
+        r2 = np.random.default_rng(seed + 1)
+        for r in sub:
+            b = bblk[r["dims"]][:r["n_rhs"]]
+            x = torch.zeros_like(b)
+            xs.append(x)
+            tk.append(srv.submit(r["gauge"], r["dims"], 1.0, r["mu"], b, x, r["n_rhs"], TOL, p,
+                                 gauge_key=1 + r["id"]))
+            if rate:
+                time.sleep(float(r2.exponential(1.0 / rate)))
+        res = [srv.wait(t) for t in tk]
+        rep = srv.report()
+        srv.close()
+        return rep, res, xs
+
+    run(reqs[:6], 0.0)                                   # warm-up: tuning of every lattice shape
+    cap, _, _ = run(reqs[:n_cap], 0.0)
+    rate = 0.7 * cap["solves_per_s"]
+    rep, res, xs = run(reqs, rate)
+    worst_res = max(x["stats"]["true_rel_resid"] for x in res)
+    # a sample of requests re-run alone: the served result must be the same, bit for bit
+    diffs = []
+    pick = [r for r in reqs if r["n_rhs"] > 1][:n_alone]
+    for r in pick:
+        k = reqs.index(r)
+        b = bblk[r["dims"]][:r["n_rhs"]]
+        op = ovl.Overlap(r["gauge"], r["dims"], 1.0, r["mu"], p)
+        xa = torch.zeros_like(b)
+        op.ovl_solve(xa, b, r["n_rhs"], TOL)
+        op.close()
+        diffs.append(((xs[k] - xa).norm() / xa.norm()).item())
+    return {"mode": "serving stream", "metric": "p50/p99 latency and solves/s of a Poisson stream of overlap solves",
+            "workload": "%d requests: V in {8^4,16^4,24^4,32^4}, mu in {0.01,0.05,0.1}, 1-12 Gaussian RHS, own 3-stout "
+                        "gauge field each, tol 1e-8, %d slots, arrivals at 0.7 x capacity" % (n_req, slots),
+            "capacity_solves_per_s": cap["solves_per_s"], "arrival_rate_per_s": rate,
+            "p50_s": rep["p50_s"], "p99_s": rep["p99_s"], "solves_per_s": rep["solves_per_s"],
+            "rhs_per_s": sum(r["n_rhs"] for r in reqs) / (len(reqs) / rep["solves_per_s"]),
+            "completed": rep["completed"], "failed": rep["failed"], "hbm_high_water_bytes": rep["hbm_high_water"],
+            "worst_true_rel_resid": worst_res, "mix_vs_alone_max_rel_diff": max(diffs) if diffs else None,
+            "alone_sample": len(diffs)}
+
+
 def cpu_baseline(budget_s=30.0):
     """The oracle as it stands on the host cores: one D_N application at the workload size
     (the definitional stencil and one plain FP64 CG per Zolotarev pole, 20 poles on the
@@ -594,6 +683,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--details", default="", help="also write the full record (every section) to this JSON file")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="instead of the solve benchmark, run the full serving stream (200 requests up to 32^4)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -606,7 +697,9 @@ def main():
             dist.init_process_group("nccl")
         else:
             dist.init_process_group("gloo")
-    if args.impl == "reference":
+    if args.serving_full:
+        out = serving_full() if rank == 0 else None
+    elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
         out = run_ours(args, rank, world, dist)

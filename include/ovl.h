@@ -71,9 +71,10 @@ typedef enum {
     OVL_ARITH_FF = 1,     /* float-float: each real is an unevaluated sum of two FP32 numbers (about
                              48 significant bits), computed on the FP32 pipes; same bytes as FP64 */
     OVL_ARITH_FP32 = 2,   /* FP32 storage and arithmetic (links stored as 12 reals) */
-    OVL_ARITH_FP16 = 3,   /* sign only: FP32 arithmetic, the multishift's shifted directions stored
-                             in FP16 with a per-site FP32 scale */
-    OVL_ARITH_BF16 = 4    /* sign only: FP32 arithmetic, shifted directions stored in BF16 */
+    OVL_ARITH_FP16 = 3,   /* FP32 arithmetic on 16-bit data. Stencil: links (12 reals) and spinors in
+                             FP16, spinors with a per-site FP32 scale. Sign: the multishift's shifted
+                             directions stored in FP16 with a per-site scale */
+    OVL_ARITH_BF16 = 4    /* as OVL_ARITH_FP16 with BF16 storage (no scale) */
 } ovl_arith;
 
 typedef enum {
@@ -310,7 +311,8 @@ typedef struct {
 
 /* Times reps back-to-back full-lattice Wilson stencil launches (out = D_W(m0_ker) in on
  * internal buffers filled with seeded pseudo-random values, after 3 untimed launches) with
- * CUDA events on the context's stream; precision 0 = FP64, 1 = FP32, 2 = float-float.
+ * CUDA events on the context's stream; precision 0 = FP64, 1 = FP32, 2 = float-float, 3 = FP16
+ * (links and spinors, per-site spinor scale; 200 algorithmic bytes per site), 4 = BF16 (192 B).
  * *ms = average milliseconds per launch. Algorithmic traffic of one launch: 96 reals per site
  * (4 links x 12, the input and the output spinor). */
 ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms);
@@ -341,8 +343,9 @@ ovl_status ovl_prof_get(ovl_ctx *ctx, ovl_prof *out, int reset);
  * FP64. OVL_EINVAL for an arithmetic the operator does not have.
  * --------------------------------------------------------------------------------- */
 
-/* out = D_W(m0) in (Eq. Wilson-Dirac) in arith = OVL_ARITH_FP64, OVL_ARITH_FF or OVL_ARITH_FP32,
- * with the context's stencil variant (params.stencil_tps; float-float always 1 thread per site). */
+/* out = D_W(m0) in (Eq. Wilson-Dirac) in any ovl_arith, with the context's stencil variant
+ * (params.stencil_tps for FP64 and FP32; float-float and 16-bit always 1 thread per site). The
+ * 16-bit stencil reads 200 B per site in FP16 (192 B in BF16) against 384 B in FP32. */
 ovl_status wilson_apply_arith(ovl_ctx *ctx, double *out, const double *in, double m0, int arith);
 
 /* out_k = D_W(m0) in_k for k < n_rhs with the multi-RHS stencil (blocks of up to 12 right-hand

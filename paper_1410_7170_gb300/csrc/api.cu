@@ -444,6 +444,25 @@ ovl_status Ctx::ensure_ff_links() {
     return OVL_OK;
 }
 
+ovl_status Ctx::ensure_16(bool bf16) {
+    Ctx *c = this;
+    const int k = bf16 ? 1 : 0;
+    if (!U16[k]) {
+        ST(alloc(&U16[k], (size_t)g.V * 4 * 3 * sizeof(uint2)));
+        CK(links_to16(g, U32, U16[k], bf16, stream));
+    }
+    if (!h16a) {
+        void *buf;
+        const size_t sp = (size_t)g.V * 3 * sizeof(uint4), nb = (size_t)g.V * sizeof(float);
+        ST(alloc(&buf, 2 * sp + 2 * nb));
+        h16a = (uint4 *)buf;
+        h16b = (uint4 *)((char *)buf + sp);
+        h16na = (float *)((char *)buf + 2 * sp);
+        h16nb = (float *)((char *)buf + 2 * sp + nb);
+    }
+    return OVL_OK;
+}
+
 ovl_status Ctx::ensure_msff() {
     ST(ensure_ff_links());
     if (msff.p) return OVL_OK;
@@ -1419,16 +1438,16 @@ extern "C" ovl_status wilson_sap_apply(ovl_ctx *ctx, double *out, const double *
 }
 
 // ------------------------------------------------------------------ operators in a chosen arithmetic
-static bool arith_ok(int a, bool sign) {
-    return a == OVL_ARITH_FP64 || a == OVL_ARITH_FF || a == OVL_ARITH_FP32 ||
-           (sign && (a == OVL_ARITH_FP16 || a == OVL_ARITH_BF16));
+static bool arith_ok(int a) {
+    return a == OVL_ARITH_FP64 || a == OVL_ARITH_FF || a == OVL_ARITH_FP32 || a == OVL_ARITH_FP16 ||
+           a == OVL_ARITH_BF16;
 }
 
 extern "C" ovl_status wilson_apply_arith(ovl_ctx *ctx, double *out, const double *in, double m0, int arith) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     ST(check_ctx_ptrs(c, out, in));
-    if (!isfinite(m0) || !arith_ok(arith, false)) {
-        c->err = "wilson_apply_arith: need finite m0 and arith OVL_ARITH_FP64, OVL_ARITH_FF or OVL_ARITH_FP32";
+    if (!isfinite(m0) || !arith_ok(arith)) {
+        c->err = "wilson_apply_arith: need finite m0 and an ovl_arith value";
         return OVL_EINVAL;
     }
     ST(c->import_vec(in, c->io_a));
@@ -1440,6 +1459,16 @@ extern "C" ovl_status wilson_apply_arith(ovl_ctx *ctx, double *out, const double
         CK(dev_d2ff(c->io_a, c->msff.t, w, c->stream));
         CK(wilson_ff(c->g, c->Uff, c->msff.t, c->msff.y, m0, 0, 1.0, nullptr, 0.0, c->stream));
         CK(dev_ff2d(c->msff.y, c->io_b, w, c->stream));
+    } else if (arith == OVL_ARITH_FP16 || arith == OVL_ARITH_BF16) {
+        // 16-bit links and spinors, FP32 arithmetic: FP64 -> FP32 -> 16 bits, stencil, and back
+        const bool bf = arith == OVL_ARITH_BF16;
+        ST(ensure_f32_buffers(c));
+        ST(c->ensure_16(bf));
+        CK(spinor_d2f(c->g, c->io_a, (float4 *)c->f_a, c->stream));
+        CK(spinor_f2h(c->g, (const float4 *)c->f_a, c->h16a, c->h16na, bf, c->stream));
+        CK(wilson_16(c->g, c->U16[bf ? 1 : 0], c->h16a, c->h16na, c->h16b, c->h16nb, (float)m0, bf, c->stream));
+        CK(spinor_h2f(c->g, c->h16b, c->h16nb, (float4 *)c->f_b, bf, c->stream));
+        CK(spinor_f2d(c->g, (const float4 *)c->f_b, c->io_b, c->stream));
     } else {
         ST(ensure_f32_buffers(c));
         CK(spinor_d2f(c->g, c->io_a, (float4 *)c->f_a, c->stream));
@@ -1490,7 +1519,7 @@ extern "C" ovl_status sign_apply_arith(ovl_ctx *ctx, double *out, const double *
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     ST(check_ctx_ptrs(c, out, in));
     ST(check_tol(c, tol));
-    if (!arith_ok(arith, true)) {
+    if (!arith_ok(arith)) {
         c->err = "sign_apply_arith: arith must be an ovl_arith value";
         return OVL_EINVAL;
     }
@@ -1534,8 +1563,12 @@ static cudaError_t fill_random(void *buf, size_t bytes, cudaStream_t st) {
 
 extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
-    if (!c || !ms || reps < 1 || precision < 0 || precision > 2) return OVL_EINVAL;
+    if (!c || !ms || reps < 1 || precision < 0 || precision > 4) return OVL_EINVAL;
     if (precision == 2) ST(c->ensure_ff_links());
+    if (precision >= 3) {
+        ST(ensure_f32_buffers(c));
+        ST(c->ensure_16(precision == 4));
+    }
     void *buf;
     ST(c->alloc(&buf, (size_t)c->n64 * sizeof(double) * 2));
     // random input spinor (floats reinterpreted: FP64 words become finite values of
@@ -1548,6 +1581,8 @@ extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, dou
     } else {
         CK(fill_random(buf, (size_t)c->n64 * sizeof(double) * 2, c->stream));
     }
+    if (precision >= 3)   // random FP32 spinor rounded to the 16-bit format
+        CK(spinor_f2h(c->g, (const float4 *)buf, c->h16a, c->h16na, precision == 4, c->stream));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1561,6 +1596,9 @@ extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, dou
         else if (precision == 2)
             e = wilson_ff(c->g, c->Uff, (const ffw *)buf, (ffw *)buf + (size_t)c->g.V * 12, c->m0_ker, 0, 1.0, nullptr,
                           0.0, c->stream);
+        else if (precision >= 3)
+            e = wilson_16(c->g, c->U16[precision - 3], c->h16a, c->h16na, c->h16b, c->h16nb, (float)c->m0_ker,
+                          precision == 4, c->stream);
         else
             e = wilson_f32(c->g, c->U32, (const float4 *)buf, (float4 *)buf + (size_t)c->g.V * 6, (float)c->m0_ker, 0,
                            1.f, nullptr, 0.f, c->stream);

@@ -259,6 +259,50 @@ __device__ __forceinline__ void load_link(const float4 *__restrict__ g, int Vh, 
     reconstruct_row2(u);
 }
 
+// 16-bit links: rows 0 and 1 of -1/2 U (12 reals) in FP16 (LinkH) or BF16 (LinkB), one
+// 8-byte word of four 16-bit reals per element, [p][mu][3][Vh] (24 B per link); row 2 is
+// rebuilt in FP32 registers. The entries of -1/2 U are bounded by 1/2, so FP16 needs no scale.
+struct __align__(8) LinkH {
+    uint32_t a, b;
+};
+struct __align__(8) LinkB {
+    uint32_t a, b;
+};
+__device__ __forceinline__ float2 unpack16(const LinkH *, uint32_t u) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&u));
+}
+__device__ __forceinline__ float2 unpack16(const LinkB *, uint32_t u) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+}
+__device__ __forceinline__ uint32_t pack16(const LinkH *, float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack16(const LinkB *, float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+template <typename R, typename L16>
+__device__ __forceinline__ void load_link16(const L16 *__restrict__ g, int Vh, int p, int mu, int i, cpx<R> u[3][3]) {
+    const uint2 *b = reinterpret_cast<const uint2 *>(g) + ((size_t)(p * 4 + mu) * 3) * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const uint2 v = __ldg(b + (size_t)c * Vh);
+        const float2 e0 = unpack16(g, v.x), e1 = unpack16(g, v.y);
+        u[(2 * c) / 3][(2 * c) % 3] = cpx<R>{(R)e0.x, (R)e0.y};
+        u[(2 * c + 1) / 3][(2 * c + 1) % 3] = cpx<R>{(R)e1.x, (R)e1.y};
+    }
+    reconstruct_row2(u);
+}
+template <typename R>
+__device__ __forceinline__ void load_link(const LinkH *__restrict__ g, int Vh, int p, int mu, int i, cpx<R> u[3][3]) {
+    load_link16<R>(g, Vh, p, mu, i, u);
+}
+template <typename R>
+__device__ __forceinline__ void load_link(const LinkB *__restrict__ g, int Vh, int p, int mu, int i, cpx<R> u[3][3]) {
+    load_link16<R>(g, Vh, p, mu, i, u);
+}
+
 // gamma_5 = diag(-1,-1,+1,+1) in the chiral basis: flips spins 0 and 1.
 template <typename R>
 __device__ __forceinline__ void apply_g5(cpx<R> s[12]) {

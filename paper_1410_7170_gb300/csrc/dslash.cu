@@ -4,6 +4,7 @@
 #include "wilson_quad.cuh"
 #include "wilson_site.cuh"
 
+#include <algorithm>
 #include <atomic>
 
 namespace ovl {
@@ -265,6 +266,87 @@ cudaError_t wilson_ff(const Geom &g, const ffw *U, const ffw *in, ffw *out, doub
                       const ffw *z, double b, cudaStream_t st) {
     const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<ff>::value, 1 << 30);
     k_wilson<ff, ffw, ffw><<<ls.grid, ls.block, 0, st>>>(g, U, in, out, ff(m0 + 4.0), g5, ff(a), z, ff(b), ls.spb);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ 16-bit stencil
+// out = D_W(m0) in with 16-bit links and 16-bit spinors (FP16 with a per-site scale, or
+// BF16), arithmetic in FP32: per site 4 x 24 B of links and the input and output spinors
+// (52 B each in FP16, 48 B in BF16) are the algorithmic traffic, about half of the FP32
+// stencil's 384 B.
+template <typename LT, typename SIn, typename SOut>
+__global__ void __launch_bounds__(kBlock, 2) k_wilson16(Geom g, const LT *__restrict__ U, SIn in, SOut out, float m4,
+                                                      int spb) {
+    const int t = blockIdx.x * spb + threadIdx.x;
+    if (threadIdx.x >= spb || t >= g.V) return;
+    int p, i;
+    site_of_thread(t, p, i);
+    cpx<float> hop[12], own[12], res[12];
+    wilson_hop<float>(g, U, in, p, i, hop);
+    load_spinor<float>(in, g.Vh, p, i, own);
+    wilson_combine<float>(m4, own, hop, res);
+    store_spinor<float>(out, g.Vh, p, i, res);
+}
+
+// FP32 links (rows 0 and 1, float4 [p][mu][3][Vh]) -> 16-bit links (uint2 [p][mu][3][Vh]):
+// every float4 word becomes one 8-byte word.
+template <typename L16>
+__global__ void k_link_to16(const float4 *__restrict__ u32, L16 *u16, long n) {
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const float4 v = u32[k];
+        reinterpret_cast<uint2 *>(u16)[k] = make_uint2(pack16(u16, v.x, v.y), pack16(u16, v.z, v.w));
+    }
+}
+// FP32 even-odd spinor <-> FP16 (per-site scale) or BF16 even-odd spinor
+template <typename S16>
+__global__ void k_spinor_f2h(Geom g, const float4 *__restrict__ a, S16 b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.V) return;
+    const int p = t >= g.Vh, i = t - p * g.Vh;
+    cpx<float> v[12];
+    load_spinor<float>(a, g.Vh, p, i, v);
+    store_spinor<float>(b, g.Vh, p, i, v);
+}
+template <typename S16C>
+__global__ void k_spinor_h2f(Geom g, S16C a, float4 *__restrict__ b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.V) return;
+    const int p = t >= g.Vh, i = t - p * g.Vh;
+    cpx<float> v[12];
+    load_spinor<float>(a, g.Vh, p, i, v);
+    store_spinor<float>(b, g.Vh, p, i, v);
+}
+
+cudaError_t links_to16(const Geom &g, const float4 *u32, void *u16, bool bf16, cudaStream_t st) {
+    const long n = (long)g.V * 4 * 3;
+    const int grid = (int)std::min<long>((n + kBlock - 1) / kBlock, 16L * g.nsm);
+    if (bf16) k_link_to16<LinkB><<<grid, kBlock, 0, st>>>(u32, (LinkB *)u16, n);
+    else k_link_to16<LinkH><<<grid, kBlock, 0, st>>>(u32, (LinkH *)u16, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t spinor_f2h(const Geom &g, const float4 *a, uint4 *v, float *norm, bool bf16, cudaStream_t st) {
+    if (bf16) k_spinor_f2h<Bf16Spinor><<<plain_grid(g.V), kBlock, 0, st>>>(g, a, Bf16Spinor{v});
+    else k_spinor_f2h<HalfSpinor><<<plain_grid(g.V), kBlock, 0, st>>>(g, a, HalfSpinor{v, norm});
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t spinor_h2f(const Geom &g, const uint4 *v, const float *norm, float4 *b, bool bf16, cudaStream_t st) {
+    if (bf16) k_spinor_h2f<Bf16SpinorC><<<plain_grid(g.V), kBlock, 0, st>>>(g, Bf16SpinorC{v}, b);
+    else k_spinor_h2f<HalfSpinorC><<<plain_grid(g.V), kBlock, 0, st>>>(g, HalfSpinorC{v, norm}, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t wilson_16(const Geom &g, const void *u16, const uint4 *in, const float *in_norm, uint4 *out, float *out_norm,
+                      float m0, bool bf16, cudaStream_t st) {
+    const LaunchShape ls = balanced_shape(g.V, g.nsm, 2, 1 << 30);
+    if (bf16)
+        k_wilson16<LinkB, Bf16SpinorC, Bf16Spinor><<<ls.grid, ls.block, 0, st>>>(
+            g, (const LinkB *)u16, Bf16SpinorC{in}, Bf16Spinor{out}, m0 + 4.f, ls.spb);
+    else
+        k_wilson16<LinkH, HalfSpinorC, HalfSpinor><<<ls.grid, ls.block, 0, st>>>(
+            g, (const LinkH *)u16, HalfSpinorC{in, in_norm}, HalfSpinor{out, out_norm}, m0 + 4.f, ls.spb);
     count_launches(1);
     return cudaGetLastError();
 }

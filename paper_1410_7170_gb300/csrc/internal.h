@@ -92,6 +92,13 @@ cudaError_t wilson_f32(const Geom &g, const float4 *U, const float4 *in, float4 
 // float-float stencil (one thread per site); links in the float-float layout of ff.cuh
 cudaError_t wilson_ff(const Geom &g, const ffw *U, const ffw *in, ffw *out, double m0, int g5, double a,
                       const ffw *z, double b, cudaStream_t st);
+// 16-bit stencil: out = D_W(m0) in with 16-bit links (from links_to16) and 16-bit spinors,
+// FP16 with a per-site scale (norm arrays of V floats) or BF16 (norms unused), FP32 arithmetic
+cudaError_t links_to16(const Geom &g, const float4 *u32, void *u16, bool bf16, cudaStream_t st);
+cudaError_t spinor_f2h(const Geom &g, const float4 *a, uint4 *v, float *norm, bool bf16, cudaStream_t st);
+cudaError_t spinor_h2f(const Geom &g, const uint4 *v, const float *norm, float4 *b, bool bf16, cudaStream_t st);
+cudaError_t wilson_16(const Geom &g, const void *u16, const uint4 *in, const float *in_norm, uint4 *out, float *out_norm,
+                      float m0, bool bf16, cudaStream_t st);
 // FP64 <-> float-float conversion of n complex words (double2 <-> ffw, same word order; used
 // for even-odd spinors and for the FP64 link array)
 cudaError_t dev_d2ff(const double2 *x, ffw *y, long n, cudaStream_t st);

@@ -83,6 +83,9 @@ struct Ctx {
     double2 *U64 = nullptr;
     float4 *U32 = nullptr;
     ffw *Uff = nullptr;           // float-float copy of U64 (made on first use)
+    void *U16[2] = {nullptr, nullptr};    // 16-bit links: FP16 [0], BF16 [1] (made on first use)
+    uint4 *h16a = nullptr, *h16b = nullptr;   // two 16-bit spinors (48 B per site)
+    float *h16na = nullptr, *h16nb = nullptr; // their per-site FP16 scales
     // boundary staging
     double *io_lex = nullptr;
     double2 *io_a = nullptr, *io_b = nullptr;
@@ -192,6 +195,7 @@ struct Ctx {
     // the FP64-accuracy sign in float-float arithmetic on FP64 even-odd vectors b, out
     ovl_status sign_ff(const double2 *b, double2 *out, double tol, int mode);
     ovl_status ensure_ff_links();
+    ovl_status ensure_16(bool bf16);   // 16-bit links of the requested type and two 16-bit spinors
     ovl_status ensure_msff();
     // FP64-accuracy sign of the outer solver: float-float in the mixed precisions when
     // params.ff_outer is set, native FP64 otherwise

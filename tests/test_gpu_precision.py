@@ -12,6 +12,8 @@ would absorb a wrong inner result as extra iterations).
 Tolerances:
   stencil, float-float: 1e-13 relative max-norm (the FP64 bar; float-float carries ~48 bits);
   stencil, FP32: 5e-7 relative max-norm (inputs rounded to 24 bits, ~50 terms per output);
+  stencil, 16-bit links and spinors: 3e-3 (FP16, 11 bits) and 2e-2 (BF16, 8 bits) relative
+  max-norm, the inputs' rounding (about 5e-4 and 4e-3 per element) summed over ~50 terms;
   sign, float-float: 1e-10 relative 2-norm at tol 1e-12 (the FP64 per-apply bar);
   sign, FP32 / FP16-stored / BF16-stored: relative 2-norm error <= 3 x the requested
   accuracy, at every accuracy down to the floor the outer solver hands that arithmetic
@@ -58,6 +60,8 @@ def rel2(a, b):
     (ovl.OVL_ARITH_FF, 1, 1e-13),
     (ovl.OVL_ARITH_FP32, 1, 5e-7),
     (ovl.OVL_ARITH_FP32, 4, 5e-7),
+    (ovl.OVL_ARITH_FP16, 1, 3e-3),
+    (ovl.OVL_ARITH_BF16, 1, 2e-2),
 ])
 @pytest.mark.parametrize("dims,ap,m0", [
     ((4, 4, 4, 4), True, -1.0),
@@ -186,7 +190,7 @@ def test_arith_arguments_rejected():
     b = dev(synth.rhs_gaussian(dims, 1))
     out = torch.empty_like(b)
     with pytest.raises(ovl.OvlError) as e:
-        op.wilson_apply_arith(out, b, -1.0, ovl.OVL_ARITH_FP16)
+        op.wilson_apply_arith(out, b, -1.0, 9)
     assert e.value.status == ovl.OVL_EINVAL
     with pytest.raises(ovl.OvlError) as e:
         op.wilson_apply_n_arith(out, b, 1, -1.0, ovl.OVL_ARITH_FF)
