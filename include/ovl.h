@@ -148,6 +148,16 @@ typedef struct {
     double max_seconds;     /* wall-clock limit of one ovl_solve call (0 = none, the default): checked on
                                the host after every chunk of multishift iterations; past it the call
                                returns OVL_ETIMEOUT (x unspecified) and the context stays usable */
+    int wilson_mg;          /* preconditioner of the FP32 Wilson FGMRES (the inexact D_W^{-1} of Sec. 5.1):
+                               0 (default) the Schwarz smoother alone; 1 the two-level aggregation
+                               multigrid the paper uses (DD-alpha-AMG, two levels, Table 2): aggregates =
+                               sap_block blocks split by chirality, mg_nv test vectors from an adaptive
+                               setup, coarse GMRES, Schwarz post-smoothing. Needs two or more blocks per
+                               direction. FP64 Wilson solves keep the Schwarz preconditioner */
+    int mg_nv;              /* test vectors (coarse dofs per aggregate; 1..24, default 12) */
+    int mg_setup_iters;     /* smoothing passes v <- v - M_SAP D_W v of the setup (default 4) */
+    int mg_coarse_steps;    /* GMRES steps of a coarse solve (1..64, default 16) */
+    double mg_coarse_tol;   /* a coarse solve stops early at this relative residual (default 0.1) */
 } ovl_params;
 
 /* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
@@ -357,6 +367,33 @@ ovl_status wilson_apply_n_arith(ovl_ctx *ctx, double *out, const double *in, int
  * about 1e-12, FP32 about 1e-6, FP16-stored directions about 1e-3, BF16-stored about 1e-2 (the
  * outer solver hands each arithmetic only requests above these floors). */
 ovl_status sign_apply_arith(ovl_ctx *ctx, double *out, const double *in, double tol, int arith);
+
+/* ---------------------------------------------------------------------------------
+ * Two-level multigrid for D_W (the Wilson solver of the paper's preconditioner, Sec. 5.1 and
+ * Table 2: two levels, red-black Schwarz smoother, adaptive setup of restriction and
+ * prolongation, GMRES on the coarse level). Aggregates are the params.sap_block blocks, each
+ * split by chirality (spins 0,1 and 2,3); P holds on every aggregate an orthonormal basis of
+ * the test vectors; D_c = P^H D_W P couples a block to itself and its eight neighbours.
+ * --------------------------------------------------------------------------------- */
+
+/* Builds the multigrid for D_W(m0). start: n_start vectors in the boundary layout (host or
+ * device) used as the initial test vectors; NULL = params.mg_nv seeded pseudo-random vectors.
+ * Each is smoothed params.mg_setup_iters times by v <- v - M_SAP D_W v, then orthonormalised on
+ * every aggregate. The setup is kept until the next call (or a solve that needs another m0).
+ * OVL_EINVAL for n_start outside [1, 24] or blocks that leave fewer than two per direction;
+ * OVL_EBREAKDOWN if a diagonal block of D_c is singular. */
+ovl_status ovl_mg_setup(ovl_ctx *ctx, double m0, const double *start, int n_start);
+
+/* out = M_MG in: one application of the two-level preconditioner for D_W(m0), FP32 inside:
+ * x = P x_c with x_c from params.mg_coarse_steps steps of GMRES on D_c x_c = P^H in (right-
+ * preconditioned by the inverses of D_c's diagonal blocks, stopping at relative residual
+ * params.mg_coarse_tol), then x += M_SAP (in - D_W x). Makes the setup first if there is none
+ * for this m0. */
+ovl_status wilson_mg_apply(ovl_ctx *ctx, double *out, const double *in, double m0);
+
+/* Multigrid state: test vectors, coarse sites, GMRES steps of the last coarse solve, setup
+ * seconds (zeros before the first setup). Nullable outputs. */
+ovl_status ovl_mg_info(const ovl_ctx *ctx, int *nv, int *coarse_sites, int *last_coarse_steps, double *setup_s);
 
 /* out = D_W(m0) in, the Wilson-Dirac operator of Eq. (Wilson-Dirac), for callers that cannot
  * allocate device memory. The paper has no counterpart to this entry point; it exists for

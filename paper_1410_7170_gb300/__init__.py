@@ -48,6 +48,8 @@ class ovl_params(ctypes.Structure):
         ("sap_tps", ctypes.c_int), ("adaptive_poles", ctypes.c_int), ("n_deflate", ctypes.c_int),
         ("deflate_tol", ctypes.c_double), ("sign_method", ctypes.c_int), ("krylov_m", ctypes.c_int),
         ("krylov_keep", ctypes.c_int), ("ff_outer", ctypes.c_int), ("max_seconds", ctypes.c_double),
+        ("wilson_mg", ctypes.c_int), ("mg_nv", ctypes.c_int), ("mg_setup_iters", ctypes.c_int),
+        ("mg_coarse_steps", ctypes.c_int), ("mg_coarse_tol", ctypes.c_double),
     ]
 
 
@@ -109,7 +111,7 @@ class ovl_prof(ctypes.Structure):
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
            "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "ovl_request_bytes", "wilson_sap_apply", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
-           "ovl_apply_n", "ovl_dslash_time_n", "wilson_apply_arith", "wilson_apply_n_arith", "sign_apply_arith", "ovl_fma_peak", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
+           "ovl_apply_n", "ovl_dslash_time_n", "wilson_apply_arith", "wilson_apply_n_arith", "sign_apply_arith", "ovl_fma_peak", "ovl_mg_setup", "wilson_mg_apply", "ovl_mg_info", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
 _lib = None
@@ -154,6 +156,9 @@ def lib():
         L.wilson_apply_n_arith.argtypes = [P, P, P, I_, D, I_]
         L.sign_apply_arith.argtypes = [P, P, P, D, I_]
         L.ovl_fma_peak.argtypes = [I_, ctypes.POINTER(D)]
+        L.ovl_mg_setup.argtypes = [P, D, P, I_]
+        L.wilson_mg_apply.argtypes = [P, P, P, D]
+        L.ovl_mg_info.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), ctypes.POINTER(I_), ctypes.POINTER(D)]
         L.ovl_server_create.argtypes = [ctypes.POINTER(P), I_, ctypes.c_size_t]
         L.ovl_server_submit.argtypes = [P, ctypes.POINTER(ovl_request), ctypes.POINTER(ctypes.c_long)]
         L.ovl_server_query.argtypes = [P, ctypes.c_long, ctypes.POINTER(ovl_result)]
@@ -260,6 +265,26 @@ def sign_apply_arith(ctx, out, inp, tol, arith):
     """out ~= sign(Q) inp to accuracy tol in any ovl_arith (FP64, FF, FP32, FP16- or BF16-stored)."""
     _check(lib().sign_apply_arith(ctx, _ptr(out, True), _ptr(inp), float(tol), int(arith)), ctx)
     return out
+
+
+def ovl_mg_setup(ctx, m0, start=None, n_start=0):
+    """Builds the two-level multigrid for D_W(m0); start: [n][V][4][3] start vectors or None."""
+    _check(lib().ovl_mg_setup(ctx, float(m0), _ptr(start) if start is not None else None,
+                              int(n_start if start is not None else 0)), ctx)
+
+
+def wilson_mg_apply(ctx, out, inp, m0):
+    """out = M_MG inp: one application of the two-level multigrid preconditioner for D_W(m0)."""
+    _check(lib().wilson_mg_apply(ctx, _ptr(out, True), _ptr(inp), float(m0)), ctx)
+    return out
+
+
+def ovl_mg_info(ctx):
+    """Test vectors, coarse sites, GMRES steps of the last coarse solve, setup seconds."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    d = ctypes.c_double()
+    _check(lib().ovl_mg_info(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), ctx)
+    return {"nv": a.value, "coarse_sites": b.value, "last_coarse_steps": c.value, "setup_s": d.value}
 
 
 def ovl_apply(ctx, out, inp, tol):
@@ -459,6 +484,15 @@ class Overlap:
 
     def ovl_apply(self, out, inp, tol):
         return ovl_apply(self.ctx, out, inp, tol)
+
+    def mg_setup(self, m0, start=None):
+        return ovl_mg_setup(self.ctx, m0, start, 0 if start is None else len(start))
+
+    def mg_apply(self, out, inp, m0):
+        return wilson_mg_apply(self.ctx, out, inp, m0)
+
+    def mg_info(self):
+        return ovl_mg_info(self.ctx)
 
     def wilson_apply_arith(self, out, inp, m0, arith):
         return wilson_apply_arith(self.ctx, out, inp, m0, arith)

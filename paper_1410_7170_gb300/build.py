@@ -15,7 +15,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libovl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["dslash.cu", "blas.cu", "multishift.cu", "solver.cu", "api.cu", "sap.cu", "multirhs.cu", "deflate.cu",
-              "krylov.cu", "noalloc.cu", "server.cu", "peak.cu"]
+              "krylov.cu", "noalloc.cu", "server.cu", "peak.cu",
+              "mg.cu", "mg_ctl.cu"]
 CXX_SOURCES = ["zolotarev.cpp", "eig_host.cpp"]
 
 

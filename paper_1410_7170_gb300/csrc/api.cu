@@ -74,6 +74,11 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->krylov_keep = 8;
     p->ff_outer = 1;
     p->max_seconds = 0.0;
+    p->wilson_mg = 0;
+    p->mg_nv = 12;
+    p->mg_setup_iters = 4;
+    p->mg_coarse_steps = 16;
+    p->mg_coarse_tol = 0.1;
     return OVL_OK;
 }
 
@@ -106,6 +111,18 @@ static ovl_status validate_params(const ovl_params &p, const int L[4], std::stri
     if (p.krylov_keep < 0 || p.krylov_keep > p.krylov_m - 2) { err = "krylov_keep must be in [0, krylov_m - 2]"; return OVL_EINVAL; }
     if (p.ff_outer != 0 && p.ff_outer != 1) { err = "ff_outer must be 0 or 1"; return OVL_EINVAL; }
     if (!(p.max_seconds >= 0)) { err = "max_seconds must be >= 0"; return OVL_EINVAL; }
+    if (p.wilson_mg != 0 && p.wilson_mg != 1) { err = "wilson_mg must be 0 or 1"; return OVL_EINVAL; }
+    if (p.mg_nv < 1 || p.mg_nv > kMgMaxNv) { err = "mg_nv must be in [1, 24]"; return OVL_EINVAL; }
+    if (p.mg_setup_iters < 0 || p.mg_setup_iters > 100) { err = "mg_setup_iters must be in [0, 100]"; return OVL_EINVAL; }
+    if (p.mg_coarse_steps < 1 || p.mg_coarse_steps > kMgMaxSteps) { err = "mg_coarse_steps must be in [1, 64]"; return OVL_EINVAL; }
+    if (!(p.mg_coarse_tol >= 0 && p.mg_coarse_tol < 1)) { err = "mg_coarse_tol must be in [0, 1)"; return OVL_EINVAL; }
+    if (p.wilson_mg) {
+        for (int m = 0; m < 4; m++)
+            if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m] || L[m] / p.sap_block[m] < 2) {
+                err = "wilson_mg needs even sap_block extents leaving at least two blocks per direction";
+                return OVL_EINVAL;
+            }
+    }
     for (int m = 0; m < 4 && p.precond != OVL_PREC_NONE; m++) {
         if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m]) {
             err = "sap_block must be even and divide the lattice extent";
@@ -1554,11 +1571,13 @@ __global__ void k_fill_random(float *x, long n, unsigned seed) {
         x[k] = (float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f;
     }
 }
-static cudaError_t fill_random(void *buf, size_t bytes, cudaStream_t st) {
-    const long n = (long)(bytes / sizeof(float));
-    k_fill_random<<<std::min<long>(4096, (n + kBlock - 1) / kBlock), kBlock, 0, st>>>((float *)buf, n, 0x9e3779b9u);
+cudaError_t ovl::fill_random_f32(float *x, long n, unsigned seed, cudaStream_t st) {
+    k_fill_random<<<std::min<long>(4096, (n + kBlock - 1) / kBlock), kBlock, 0, st>>>(x, n, seed);
     count_launches(1);
     return cudaGetLastError();
+}
+static cudaError_t fill_random(void *buf, size_t bytes, cudaStream_t st) {
+    return fill_random_f32((float *)buf, (long)(bytes / sizeof(float)), 0x9e3779b9u, st);
 }
 
 extern "C" ovl_status ovl_dslash_time(ovl_ctx *ctx, int precision, int reps, double *ms) {

@@ -137,6 +137,8 @@ cudaError_t dev_orth_scale_f(const float *base, long stride, int m, const double
                              float *out, long n, cudaStream_t st);
 cudaError_t dev_multiaxpy_f(const float *base, long stride, int m, const double *c, float *w, long n,
                             cudaStream_t st);
+// x[k] = seeded pseudo-random values in [-1, 1) (a counter hash of k and the seed)
+cudaError_t fill_random_f32(float *x, long n, unsigned seed, cudaStream_t st);
 // Finite check of a flat array: *flag = 1 if some entry is NaN/Inf.
 cudaError_t dev_nonfinite(const double *x, long n, int *flag, cudaStream_t st);
 

@@ -300,6 +300,7 @@ static ovl_status wilson_solve(Ctx *c, Krylov<T> &k, const T *in, T *out, double
         return OVL_OK;
     };
     auto pc = [&](const T *a, T *o) -> ovl_status {
+        if (sizeof(T) == 4 && c->p.wilson_mg) return mg_apply_f32(c, (const float4 *)a, (float4 *)o, m0);
         CK(Ops<T>::sap(c, sg, a, o, scratch, m0));
         return OVL_OK;
     };
@@ -800,9 +801,12 @@ ovl_status wilson_solve_batch(Ctx *c, int nb, const T *in, T *out, double m0, do
         return OVL_OK;
     };
     auto pc = [&](const T *a, T *o, const char *act) -> ovl_status {
-        for (int y = 0; y < nb; y++)
-            if (act[y]) CK(Ops<T>::sap(c, sg, a + (long)y * n, o + (long)y * n, scratch, m0));
-            else CK(cudaMemsetAsync(o + (long)y * n, 0, n * sizeof(T), c->stream));
+        for (int y = 0; y < nb; y++) {
+            if (!act[y]) CK(cudaMemsetAsync(o + (long)y * n, 0, n * sizeof(T), c->stream));
+            else if (sizeof(T) == 4 && c->p.wilson_mg)
+                ST(mg_apply_f32(c, (const float4 *)(a + (long)y * n), (float4 *)(o + (long)y * n), m0));
+            else CK(Ops<T>::sap(c, sg, a + (long)y * n, o + (long)y * n, scratch, m0));
+        }
         return OVL_OK;
     };
     int its;

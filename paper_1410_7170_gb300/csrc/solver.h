@@ -7,6 +7,7 @@
 
 #include "../../include/ovl.h"
 #include "internal.h"
+#include "mg.h"
 
 namespace ovl {
 
@@ -160,6 +161,8 @@ struct Ctx {
     double2 *ks_f = nullptr, *ks_tmp = nullptr;       // accumulated f(Q^2) Q b, stencil scratch
     double *ks_S = nullptr;                           // Ritz coefficients (device)
     long ks_cycles = 0, ks_matvecs = 0;               // totals since creation
+    // two-level multigrid for the Wilson solves (params.wilson_mg)
+    MgData mg;
     // batches of several right-hand sides sized by params.rhs_block alone, not by the free
     // device memory (set by the serving loop, which reserves that memory at admission, so
     // that a request's batching does not depend on what else is running)
@@ -254,5 +257,10 @@ ovl_status solve_batch(Ctx *c, double2 *x, const double2 *b, int nrhs, double to
 ovl_status wilson_solve_eo(Ctx *c, const double2 *b, double2 *x, double m0, double tol, int *iters);
 // One Schwarz preconditioner application x = M_SAP b on FP64 even-odd spinors.
 ovl_status sap_apply_eo(Ctx *c, const double2 *b, double2 *x, double m0);
+// Two-level multigrid for D_W(m0) (mg_ctl.cu): setup from n_start start vectors (boundary
+// layout; NULL = seeded pseudo-random ones), and one preconditioner application on FP32
+// even-odd spinors (the setup is made, or remade for a new m0, first).
+ovl_status mg_setup(Ctx *c, double m0, const double *start, int n_start);
+ovl_status mg_apply_f32(Ctx *c, const float4 *r, float4 *x, double m0);
 
 }  // namespace ovl
