@@ -164,6 +164,7 @@ Ctx::~Ctx() {
     if (stream) cudaStreamSynchronize(stream);
     for (auto &gr : graphs)
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (mg.graph) cudaGraphExecDestroy(mg.graph);
     for (int w = 0; w < 3; w++)
         if (ev_ready[w])
             for (int k = 0; k < 4; k++) cudaEventDestroy(ev[w][k]);

@@ -393,10 +393,12 @@ __global__ void __launch_bounds__(64) k_mgc_init(MgData mg, int m, double tol) {
     }
 }
 
-// step j: v_j = scale * src (own block written to V[j]); w = A v_j; H[i][j] = <v_i, w>, i <= j
+// step j: v_j = scale * src (own block written to V[j]); w = A v_j; H[i][j] = <v_i, w>, i <= j.
+// The partial dots of a block need no reduction across threads: w and v_j go to shared memory
+// and thread i sums <v_i, w> over the block's nc entries.
 __global__ void __launch_bounds__(64) k_mgc_arnoldi(MgData mg) {
     __shared__ float2 xs[9][2 * kMgMaxNv];
-    __shared__ double sm[8][2];
+    __shared__ float2 ws[2 * kMgMaxNv], vs[2 * kMgMaxNv];
     MgCoarseState *cs = mg.cs;
     if (cs->done) return;
     const int j = cs->j, b = blockIdx.x, t = threadIdx.x, nc = mg.nc;
@@ -404,26 +406,28 @@ __global__ void __launch_bounds__(64) k_mgc_arnoldi(MgData mg) {
     const float2 *src = j == 0 ? mg.rc : mg.w[(j - 1) & 1];
     float2 *w = mg.w[j & 1];
     const long at = (long)b * nc + t;
-    float2 vj = make_float2(0.f, 0.f);
     if (t < nc) {
         const float2 s = src[at];
-        vj = make_float2(scale * s.x, scale * s.y);
+        const float2 vj = make_float2(scale * s.x, scale * s.y);
         mg.V[(long)j * mg.ncv + at] = vj;
+        vs[t] = vj;
     }
     const float2 r = coarse_row(mg.A, mg.nbr, src, scale, b, nc, xs);
-    if (t < nc) w[at] = r;
-    for (int i = 0; i <= j; i++) {
+    if (t < nc) {
+        w[at] = r;
+        ws[t] = r;
+    }
+    __syncthreads();
+    if (t <= j) {
+        const float2 *vi = mg.V + (long)t * mg.ncv + (long)b * nc;
         float re = 0.f, im = 0.f;
-        if (t < nc) {
-            const float2 v = i == j ? vj : mg.V[(long)i * mg.ncv + at];
-            re = v.x * r.x + v.y * r.y;
-            im = v.x * r.y - v.y * r.x;
+        for (int e = 0; e < nc; e++) {
+            const float2 v = t == j ? vs[e] : vi[e], x = ws[e];
+            re += v.x * x.x + v.y * x.y;
+            im += v.x * x.y - v.y * x.x;
         }
-        const cpx<double> d = block_csum(re, im, sm);
-        if (t == 0) {
-            mg.part[(2 * i) * mg.nb + b] = d.re;
-            mg.part[(2 * i + 1) * mg.nb + b] = d.im;
-        }
+        mg.part[(2 * t) * mg.nb + b] = re;
+        mg.part[(2 * t + 1) * mg.nb + b] = im;
     }
     if (last_cta(mg.counter)) {
         for (int i = t; i <= j; i += blockDim.x) {

@@ -25,7 +25,7 @@ struct MgCoarseState {
     double tol;             // stop when the residual estimate <= tol * beta0
     double beta0;
     float scale;            // 1 / norm of the vector that becomes v_j
-    double H[(kMgMaxSteps + 1) * kMgMaxSteps * 2];   // Hessenberg, complex, column j at [(j*(m+1)+i)*2]
+    double H[(kMgMaxSteps + 1) * kMgMaxSteps * 2];   // Hessenberg, complex, H(i, j) at [(j*(kMgMaxSteps+1)+i)*2]
     double g[(kMgMaxSteps + 1) * 2];                 // rotated right-hand side, complex
     double cs[kMgMaxSteps];                          // Givens cosines (real)
     double sn[kMgMaxSteps * 2];                      // Givens sines (complex)
@@ -47,6 +47,9 @@ struct MgData {
     unsigned *counter = nullptr;    // last-block counter
     MgCoarseState *cs = nullptr;
     float4 *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;   // fine FP32 scratch spinors
+    float4 *tin = nullptr, *tout = nullptr;               // fixed input / output of the captured application
+    cudaGraphExec_t graph = nullptr;   // one application captured as a CUDA graph (rebuilt with the setup)
+    long graph_launches = 0;           // kernels in that graph
     double m0 = 0;                  // mass the setup was made for
     bool ready = false;
     double setup_s = 0;

@@ -92,6 +92,7 @@ ovl_status mg_alloc(Ctx *c, int nv) {
     MgData &mg = c->mg;
     if (mg.P && mg.nv == nv) return OVL_OK;
     if (mg.P) {   // a different number of test vectors: drop the old workspace
+        if (mg.graph) cudaGraphExecDestroy(mg.graph);
         void *ptrs[] = {mg.P, mg.Dc, mg.A, mg.Minv, mg.nbr, mg.V, mg.w[0], mg.rc, mg.part, mg.cs, mg.t1};
         for (void *q : ptrs) {
             cudaFree(q);
@@ -130,10 +131,12 @@ ovl_status mg_alloc(Ctx *c, int nv) {
     mg.counter = (unsigned *)((char *)b + (size_t)2 * (kMgMaxSteps + 2) * mg.nb * sizeof(double));
     ST(c->alloc(&b, sizeof(MgCoarseState)));
     mg.cs = (MgCoarseState *)b;
-    ST(c->alloc(&b, vs * 3));
+    ST(c->alloc(&b, vs * 5));
     mg.t1 = (float4 *)b;
     mg.t2 = mg.t1 + (size_t)c->g.V * 6;
     mg.t3 = mg.t2 + (size_t)c->g.V * 6;
+    mg.tin = mg.t3 + (size_t)c->g.V * 6;
+    mg.tout = mg.tin + (size_t)c->g.V * 6;
     CK(cudaMemsetAsync(mg.counter, 0, sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(mg.cs, 0, sizeof(MgCoarseState), c->stream));
     return OVL_OK;
@@ -148,6 +151,10 @@ ovl_status mg_setup(Ctx *c, double m0, const double *start, int n_start) {
     ST(mg_alloc(c, nv));
     MgData &mg = c->mg;
     mg.ready = false;
+    if (mg.graph) {   // the captured application holds the old setup's mass
+        cudaGraphExecDestroy(mg.graph);
+        mg.graph = nullptr;
+    }
     const Geom &g = c->g;
     SapGeom sg = make_sap_geom(g, c->p.sap_block);
     sg.tps = c->sap_tps;
@@ -231,19 +238,55 @@ ovl_status mg_setup(Ctx *c, double m0, const double *start, int n_start) {
     return OVL_OK;
 }
 
-ovl_status mg_apply_f32(Ctx *c, const float4 *r, float4 *x, double m0) {
-    if (!c->mg.ready || c->mg.m0 != m0) ST(mg_setup(c, m0, nullptr, 0));
+// The kernels of one application, from r to x.
+static cudaError_t mg_apply_kernels(Ctx *c, const float4 *r, float4 *x, double m0) {
     MgData &mg = c->mg;
     const Geom &g = c->g;
     SapGeom sg = make_sap_geom(g, c->p.sap_block);
     sg.tps = c->sap_tps;
     cudaStream_t st = c->stream;
-    CK(mg_restrict(g, sg, mg.P, mg.nv, r, mg.rc, mg.nc, 0, st));
-    CK(mg_coarse_solve(mg, c->p.mg_coarse_steps, c->p.mg_coarse_tol, st));
-    CK(mg_prolong(g, sg, mg.P, mg.nv, mg.xc, x, false, st));
-    CK(wilson_f32(g, c->U32, x, mg.t1, (float)m0, 0, -1.f, r, 1.f, st));   // r - D_W x
-    CK(sap_f32(g, sg, c->U32, mg.t1, mg.t2, mg.t3, (float)m0, c->p.sap_cycles, c->p.sap_mr_iters, st));
-    CK(dev_axpby_f(1.f, (const float *)mg.t2, 1.f, (float *)x, (long)g.V * 24, st));
+    cudaError_t e;
+    if ((e = mg_restrict(g, sg, mg.P, mg.nv, r, mg.rc, mg.nc, 0, st)) != cudaSuccess) return e;
+    if ((e = mg_coarse_solve(mg, c->p.mg_coarse_steps, c->p.mg_coarse_tol, st)) != cudaSuccess) return e;
+    if ((e = mg_prolong(g, sg, mg.P, mg.nv, mg.xc, x, false, st)) != cudaSuccess) return e;
+    if ((e = wilson_f32(g, c->U32, x, mg.t1, (float)m0, 0, -1.f, r, 1.f, st)) != cudaSuccess) return e;   // r - D_W x
+    if ((e = sap_f32(g, sg, c->U32, mg.t1, mg.t2, mg.t3, (float)m0, c->p.sap_cycles, c->p.sap_mr_iters, st)) !=
+        cudaSuccess)
+        return e;
+    return dev_axpby_f(1.f, (const float *)mg.t2, 1.f, (float *)x, (long)g.V * 24, st);
+}
+
+// One application. The application's some 40 short kernels are captured once per setup as a
+// CUDA graph on fixed input and output buffers (the caller's vectors are copied in and out),
+// so that a Wilson FGMRES iteration pays one graph launch instead of 40 kernel launches.
+ovl_status mg_apply_f32(Ctx *c, const float4 *r, float4 *x, double m0) {
+    if (!c->mg.ready || c->mg.m0 != m0) ST(mg_setup(c, m0, nullptr, 0));
+    MgData &mg = c->mg;
+    cudaStream_t st = c->stream;
+    const size_t bytes = (size_t)c->g.V * 6 * sizeof(float4);
+    if (!c->p.use_graphs) {
+        CK(mg_apply_kernels(c, r, x, m0));
+        mg.applications++;
+        return OVL_OK;
+    }
+    if (!mg.graph) {
+        const long before = launches_total();
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t ce = mg_apply_kernels(c, mg.tin, mg.tout, m0);
+        const cudaError_t ee = cudaStreamEndCapture(st, &graph);
+        mg.graph_launches = launches_total() - before;
+        count_launches(-mg.graph_launches);   // captured, not run
+        CK(ce);
+        CK(ee);
+        const cudaError_t ie = cudaGraphInstantiate(&mg.graph, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+    }
+    CK(cudaMemcpyAsync(mg.tin, r, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaGraphLaunch(mg.graph, st));
+    count_launches(mg.graph_launches);
+    CK(cudaMemcpyAsync(x, mg.tout, bytes, cudaMemcpyDeviceToDevice, st));
     mg.applications++;
     return OVL_OK;
 }
