@@ -62,56 +62,39 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-constexpr int kChunk = 8;   // test vectors per reduction round of the restriction
-
-// out[B * ob + off + chi * nv + k] = <P_k restricted to aggregate (B, chi), r>
+// out[B * ob + off + chi * nv + k] = <P_k restricted to aggregate (B, chi), r>: one CTA per
+// (block B, test vector k), one thread per block site, one block-wide sum of two complex numbers.
 __global__ void __launch_bounds__(256) k_mg_restrict(Geom g, SapGeom sg, const float4 *__restrict__ P, int nv,
                                                      const float4 *__restrict__ r, float2 *__restrict__ out, long ob,
                                                      long off) {
-    __shared__ float red[8][kChunk * 4];
-    const int B = blockIdx.x, l = threadIdx.x, lane = l & 31, warp = l >> 5, nw = (blockDim.x + 31) >> 5;
-    const bool active = l < sg.nb;
-    int p = 0, i = 0, x[4];
-    cpx<float> rv[12];
-    if (active) {
+    __shared__ float red[8][4];
+    const int B = blockIdx.x, k = blockIdx.y, l = threadIdx.x, lane = l & 31, warp = l >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (l < sg.nb) {
+        int p, i, x[4];
         block_site(g, sg, B, l, p, i, x);
+        cpx<float> rv[12], pv[12];
         load_spinor<float>(r, g.Vh, p, i, rv);
+        load_spinor<float>(P + (long)k * g.V * 6, g.Vh, p, i, pv);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            const int h = c < 6 ? 0 : 2;
+            acc[h] += pv[c].re * rv[c].re + pv[c].im * rv[c].im;
+            acc[h + 1] += pv[c].re * rv[c].im - pv[c].im * rv[c].re;
+        }
     }
-    const long vs = (long)g.V * 6;
-    for (int k0 = 0; k0 < nv; k0 += kChunk) {
-        float acc[kChunk * 4];
 #pragma unroll
-        for (int u = 0; u < kChunk * 4; u++) acc[u] = 0.f;
-#pragma unroll
-        for (int u = 0; u < kChunk; u++) {
-            const int k = k0 + u;
-            if (!active || k >= nv) continue;
-            cpx<float> pv[12];
-            load_spinor<float>(P + k * vs, g.Vh, p, i, pv);
-#pragma unroll
-            for (int c = 0; c < 12; c++) {
-                const int h = c < 6 ? 0 : 2;
-                acc[u * 4 + h] += pv[c].re * rv[c].re + pv[c].im * rv[c].im;
-                acc[u * 4 + h + 1] += pv[c].re * rv[c].im - pv[c].im * rv[c].re;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kChunk * 4; u++) {
-            const float s = warp_sum_f(acc[u]);
-            if (lane == 0) red[warp][u] = s;
-        }
-        __syncthreads();
-        if (l < kChunk * 4) {
-            float s = 0.f;
-            for (int w = 0; w < nw; w++) s += red[w][l];
-            const int u = l >> 2, h = l & 3, k = k0 + u;
-            if (k < nv) {
-                const int chi = h >> 1;
-                float *o = reinterpret_cast<float *>(out + B * ob + off + chi * nv + k);
-                o[h & 1] = s;
-            }
-        }
-        __syncthreads();
+    for (int u = 0; u < 4; u++) {
+        const float s = warp_sum_f(acc[u]);
+        if (lane == 0) red[warp][u] = s;
+    }
+    __syncthreads();
+    if (l < 4) {
+        float s = 0.f;
+        for (int w = 0; w < nw; w++) s += red[w][l];
+        float *o = reinterpret_cast<float *>(out + B * ob + off + (l >> 1) * nv + k);
+        o[l & 1] = s;
     }
 }
 
@@ -316,35 +299,45 @@ __global__ void __launch_bounds__(256) k_mg_rightprec(const float2 *__restrict__
     }
 }
 
-// y[b] = sum_d Op[b][d] (scale * x[nbr[b][d]]); one CTA per coarse site, thread = row
+constexpr int kCoarseThreads = 9 * 2 * kMgMaxNv;   // one thread per (direction, row)
+
+// y[b] = sum_d Op[b][d] (scale * x[nbr[b][d]]); one CTA per coarse site. Thread (d, row) forms
+// the product of one nc x nc block with one neighbour's vector (nc terms); the nine partial
+// rows are then summed. Returns the row for threads < nc (others: 0). Every thread calls it.
 __device__ __forceinline__ float2 coarse_row(const float2 *__restrict__ Op, const int *__restrict__ nbr,
                                              const float2 *__restrict__ x, float scale, int b, int nc,
-                                             float2 (*xs)[2 * kMgMaxNv]) {
+                                             float2 (*xs)[2 * kMgMaxNv], float2 (*ps)[2 * kMgMaxNv]) {
     const int t = threadIdx.x;
-    for (int e = t; e < 9 * nc; e += blockDim.x) {
-        const int d = e / nc, col = e % nc;
-        const float2 v = x[(long)nbr[b * 9 + d] * nc + col];
-        xs[d][col] = make_float2(scale * v.x, scale * v.y);
+    const int d = t / nc, row = t - d * nc;
+    if (d < 9) {
+        const float2 v = x[(long)nbr[b * 9 + d] * nc + row];
+        xs[d][row] = make_float2(scale * v.x, scale * v.y);
+    }
+    __syncthreads();
+    if (d < 9) {
+        const float2 *O = Op + ((long)b * 9 + d) * nc * nc;
+        float re = 0.f, im = 0.f;
+        for (int col = 0; col < nc; col++) {
+            const float2 a = O[col * nc + row], v = xs[d][col];
+            re += a.x * v.x - a.y * v.y;
+            im += a.x * v.y + a.y * v.x;
+        }
+        ps[d][row] = make_float2(re, im);
     }
     __syncthreads();
     float re = 0.f, im = 0.f;
-    if (t < nc) {
-        for (int d = 0; d < 9; d++) {
-            const float2 *O = Op + ((long)b * 9 + d) * nc * nc;
-            for (int col = 0; col < nc; col++) {
-                const float2 a = O[col * nc + t], v = xs[d][col];
-                re += a.x * v.x - a.y * v.y;
-                im += a.x * v.y + a.y * v.x;
-            }
+    if (t < nc)
+        for (int e = 0; e < 9; e++) {
+            re += ps[e][t].x;
+            im += ps[e][t].y;
         }
-    }
     return make_float2(re, im);
 }
 
-__global__ void __launch_bounds__(64) k_mg_coarse_apply(const float2 *Op, const int *nbr, const float2 *x, float2 *y,
-                                                        int nc) {
-    __shared__ float2 xs[9][2 * kMgMaxNv];
-    const float2 r = coarse_row(Op, nbr, x, 1.f, blockIdx.x, nc, xs);
+__global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse_apply(const float2 *Op, const int *nbr, const float2 *x,
+                                                                    float2 *y, int nc) {
+    __shared__ float2 xs[9][2 * kMgMaxNv], ps[9][2 * kMgMaxNv];
+    const float2 r = coarse_row(Op, nbr, x, 1.f, blockIdx.x, nc, xs, ps);
     if (threadIdx.x < nc) y[(long)blockIdx.x * nc + threadIdx.x] = r;
 }
 
@@ -396,8 +389,8 @@ __global__ void __launch_bounds__(64) k_mgc_init(MgData mg, int m, double tol) {
 // step j: v_j = scale * src (own block written to V[j]); w = A v_j; H[i][j] = <v_i, w>, i <= j.
 // The partial dots of a block need no reduction across threads: w and v_j go to shared memory
 // and thread i sums <v_i, w> over the block's nc entries.
-__global__ void __launch_bounds__(64) k_mgc_arnoldi(MgData mg) {
-    __shared__ float2 xs[9][2 * kMgMaxNv];
+__global__ void __launch_bounds__(kCoarseThreads) k_mgc_arnoldi(MgData mg) {
+    __shared__ float2 xs[9][2 * kMgMaxNv], ps[9][2 * kMgMaxNv];
     __shared__ float2 ws[2 * kMgMaxNv], vs[2 * kMgMaxNv];
     MgCoarseState *cs = mg.cs;
     if (cs->done) return;
@@ -412,7 +405,7 @@ __global__ void __launch_bounds__(64) k_mgc_arnoldi(MgData mg) {
         mg.V[(long)j * mg.ncv + at] = vj;
         vs[t] = vj;
     }
-    const float2 r = coarse_row(mg.A, mg.nbr, src, scale, b, nc, xs);
+    const float2 r = coarse_row(mg.A, mg.nbr, src, scale, b, nc, xs, ps);
     if (t < nc) {
         w[at] = r;
         ws[t] = r;
@@ -567,7 +560,7 @@ inline int round32(int n) { return (n + 31) / 32 * 32; }
 cudaError_t mg_restrict(const Geom &g, const SapGeom &sg, const float4 *P, int nv, const float4 *r, float2 *out,
                         long ob, long off, cudaStream_t st) {
     const int nb = sg.nblk[0] * sg.nblk[1] * sg.nblk[2] * sg.nblk[3];
-    k_mg_restrict<<<nb, round32(sg.nb), 0, st>>>(g, sg, P, nv, r, out, ob, off);
+    k_mg_restrict<<<dim3(nb, nv), round32(sg.nb), 0, st>>>(g, sg, P, nv, r, out, ob, off);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -603,14 +596,14 @@ cudaError_t mg_right_precondition(const MgData &mg, cudaStream_t st) {
     return cudaGetLastError();
 }
 cudaError_t mg_coarse_apply(const MgData &mg, const float2 *x, float2 *y, cudaStream_t st) {
-    k_mg_coarse_apply<<<mg.nb, 64, 0, st>>>(mg.Dc, mg.nbr, x, y, mg.nc);
+    k_mg_coarse_apply<<<mg.nb, kCoarseThreads, 0, st>>>(mg.Dc, mg.nbr, x, y, mg.nc);
     count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t mg_coarse_solve(const MgData &mg, int m, double tol, cudaStream_t st) {
     k_mgc_init<<<mg.nb, 64, 0, st>>>(mg, m, tol);
     for (int j = 0; j < m; j++) {
-        k_mgc_arnoldi<<<mg.nb, 64, 0, st>>>(mg);
+        k_mgc_arnoldi<<<mg.nb, kCoarseThreads, 0, st>>>(mg);
         k_mgc_orth<<<mg.nb, 64, 0, st>>>(mg);
     }
     k_mgc_final<<<mg.nb, 64, 0, st>>>(mg);
