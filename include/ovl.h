@@ -158,6 +158,12 @@ typedef struct {
     int mg_setup_iters;     /* smoothing passes v <- v - M_SAP D_W v of the setup (default 4) */
     int mg_coarse_steps;    /* GMRES steps of a coarse solve (1..64, default 16) */
     double mg_coarse_tol;   /* a coarse solve stops early at this relative residual (default 0.1) */
+    int m0_adapt;           /* 1: choose the Wilson preconditioner mass of the inner FGMRES (precond =
+                               OVL_PREC_RECURSIVE, one right-hand side at a time) on the fly, from one
+                               FGMRES iteration to the next (Sec. 5.1): five candidates over
+                               [1.5 m0_prec, 0.5 m0_prec], each scored by the drop of the residual
+                               estimate per second of the iteration it served; the scores persist in
+                               the context across solves. 0 (default): always m0_prec */
 } ovl_params;
 
 /* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
@@ -390,6 +396,12 @@ ovl_status ovl_mg_setup(ovl_ctx *ctx, double m0, const double *start, int n_star
  * params.mg_coarse_tol), then x += M_SAP (in - D_W x). Makes the setup first if there is none
  * for this m0. */
 ovl_status wilson_mg_apply(ovl_ctx *ctx, double *out, const double *in, double m0);
+
+/* State of the on-the-fly preconditioner mass (params.m0_adapt): the candidate masses cand[5],
+ * their scores (credited residual drop per second; 0 before use) eff[5], the number of
+ * preconditioner applications made so far, and the best candidate (NaN before any score).
+ * Nullable outputs. */
+ovl_status ovl_m0_adapt_info(const ovl_ctx *ctx, double *cand, double *eff, long *uses, double *best);
 
 /* Multigrid state: test vectors, coarse sites, GMRES steps of the last coarse solve, setup
  * seconds (zeros before the first setup). Nullable outputs. */

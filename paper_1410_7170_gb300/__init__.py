@@ -49,7 +49,7 @@ class ovl_params(ctypes.Structure):
         ("deflate_tol", ctypes.c_double), ("sign_method", ctypes.c_int), ("krylov_m", ctypes.c_int),
         ("krylov_keep", ctypes.c_int), ("ff_outer", ctypes.c_int), ("max_seconds", ctypes.c_double),
         ("wilson_mg", ctypes.c_int), ("mg_nv", ctypes.c_int), ("mg_setup_iters", ctypes.c_int),
-        ("mg_coarse_steps", ctypes.c_int), ("mg_coarse_tol", ctypes.c_double),
+        ("mg_coarse_steps", ctypes.c_int), ("mg_coarse_tol", ctypes.c_double), ("m0_adapt", ctypes.c_int),
     ]
 
 
@@ -111,7 +111,7 @@ class ovl_prof(ctypes.Structure):
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
            "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "ovl_request_bytes", "wilson_sap_apply", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
-           "ovl_apply_n", "ovl_dslash_time_n", "wilson_apply_arith", "wilson_apply_n_arith", "sign_apply_arith", "ovl_fma_peak", "ovl_mg_setup", "wilson_mg_apply", "ovl_mg_info", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
+           "ovl_apply_n", "ovl_dslash_time_n", "wilson_apply_arith", "wilson_apply_n_arith", "sign_apply_arith", "ovl_fma_peak", "ovl_mg_setup", "wilson_mg_apply", "ovl_mg_info", "ovl_m0_adapt_info", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
 _lib = None
@@ -159,6 +159,7 @@ def lib():
         L.ovl_mg_setup.argtypes = [P, D, P, I_]
         L.wilson_mg_apply.argtypes = [P, P, P, D]
         L.ovl_mg_info.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), ctypes.POINTER(I_), ctypes.POINTER(D)]
+        L.ovl_m0_adapt_info.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(D)]
         L.ovl_server_create.argtypes = [ctypes.POINTER(P), I_, ctypes.c_size_t]
         L.ovl_server_submit.argtypes = [P, ctypes.POINTER(ovl_request), ctypes.POINTER(ctypes.c_long)]
         L.ovl_server_query.argtypes = [P, ctypes.c_long, ctypes.POINTER(ovl_result)]
@@ -285,6 +286,16 @@ def ovl_mg_info(ctx):
     d = ctypes.c_double()
     _check(lib().ovl_mg_info(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), ctx)
     return {"nv": a.value, "coarse_sites": b.value, "last_coarse_steps": c.value, "setup_s": d.value}
+
+
+def ovl_m0_adapt_info(ctx):
+    """Candidate preconditioner masses, their scores, applications so far and the best mass."""
+    import numpy as np
+    cand = np.zeros(5)
+    eff = np.zeros(5)
+    uses, best = ctypes.c_long(), ctypes.c_double()
+    _check(lib().ovl_m0_adapt_info(ctx, _ptr(cand, True), _ptr(eff, True), ctypes.byref(uses), ctypes.byref(best)), ctx)
+    return {"cand": cand.tolist(), "eff": eff.tolist(), "uses": uses.value, "best": best.value}
 
 
 def ovl_apply(ctx, out, inp, tol):
@@ -493,6 +504,9 @@ class Overlap:
 
     def mg_info(self):
         return ovl_mg_info(self.ctx)
+
+    def m0_adapt_info(self):
+        return ovl_m0_adapt_info(self.ctx)
 
     def wilson_apply_arith(self, out, inp, m0, arith):
         return wilson_apply_arith(self.ctx, out, inp, m0, arith)

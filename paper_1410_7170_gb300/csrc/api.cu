@@ -79,6 +79,7 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->mg_setup_iters = 4;
     p->mg_coarse_steps = 16;
     p->mg_coarse_tol = 0.1;
+    p->m0_adapt = 0;
     return OVL_OK;
 }
 
@@ -116,6 +117,7 @@ static ovl_status validate_params(const ovl_params &p, const int L[4], std::stri
     if (p.mg_setup_iters < 0 || p.mg_setup_iters > 100) { err = "mg_setup_iters must be in [0, 100]"; return OVL_EINVAL; }
     if (p.mg_coarse_steps < 1 || p.mg_coarse_steps > kMgMaxSteps) { err = "mg_coarse_steps must be in [1, 64]"; return OVL_EINVAL; }
     if (!(p.mg_coarse_tol >= 0 && p.mg_coarse_tol < 1)) { err = "mg_coarse_tol must be in [0, 1)"; return OVL_EINVAL; }
+    if (p.m0_adapt != 0 && p.m0_adapt != 1) { err = "m0_adapt must be 0 or 1"; return OVL_EINVAL; }
     if (p.wilson_mg) {
         for (int m = 0; m < 4; m++)
             if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m] || L[m] / p.sap_block[m] < 2) {
@@ -1387,6 +1389,26 @@ extern "C" ovl_status ovl_krylov_sign_info(const ovl_ctx *ctx, long *cycles, lon
     const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
     if (cycles) *cycles = c->ks_cycles;
     if (matvecs) *matvecs = c->ks_matvecs;
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_m0_adapt_info(const ovl_ctx *ctx, double *cand, double *eff, long *uses, double *best) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c) return OVL_EINVAL;
+    const Ctx::M0Adapt &a = c->m0a;
+    double b = NAN, be = 0.0;
+    for (int k = 0; k < 5; k++) {
+        const bool have = k < (int)a.cand.size();
+        const double e = have && a.cost[k] > 0 ? a.gain[k] / a.cost[k] : 0.0;
+        if (cand) cand[k] = have ? a.cand[k] : 0.0;
+        if (eff) eff[k] = e;
+        if (have && e > be) {
+            be = e;
+            b = a.cand[k];
+        }
+    }
+    if (uses) *uses = a.uses;
+    if (best) *best = b;
     return OVL_OK;
 }
 

@@ -176,6 +176,7 @@ static ovl_status fgmres(Ctx *c, Krylov<T> &k, T *x, const T *b, double tol, int
             T *zj = vj;
             if (precond) {
                 zj = k.Z + (long)j * n;
+                c->fgmres_rel = std::abs(gv[j]) / bnorm;   // read by an adaptive preconditioner
                 ST((*precond)(vj, zj));
             }
             const double rel_now = std::abs(gv[j]) / bnorm;
@@ -317,6 +318,57 @@ static double relax_tol(Ctx *c, double target, double rel_now, double lo, double
     return std::min(hi, std::max(lo, e));
 }
 
+// Wilson preconditioner mass for the next inner FGMRES iteration (params.m0_adapt), Sec. 5.1:
+// the paper observes that the best m0_prec is not known a priori and suggests approximating
+// it "on the fly" by changing it from one preconditioned FGMRES iteration to the next, without
+// a rule. Reading: five candidates spread over [1.5 m0_def, 0.5 m0_def]; the application made
+// with candidate i is credited, once the next iteration starts, with the drop of the FGMRES
+// residual estimate, -log(r_new / r_old), and with the wall time in between (its Wilson solve
+// and the D_N product of that iteration). Each candidate is tried twice, then the one with the
+// largest credited drop per second is used, with a random candidate one time in eight.
+static double m0_adapt_pick(Ctx *c, double rel_now) {
+    Ctx::M0Adapt &a = c->m0a;
+    const auto now = std::chrono::steady_clock::now();
+    if (a.cand.empty()) {
+        const double m = c->m0_prec;
+        for (int k = 0; k < 5; k++) a.cand.push_back(m * (1.5 - 0.25 * k));
+        a.gain.assign(5, 0.0);
+        a.cost.assign(5, 0.0);
+        a.n.assign(5, 0);
+    }
+    if (a.pending >= 0 && rel_now > 0 && a.rel_pending > 0) {
+        a.gain[a.pending] += std::max(0.0, -log(rel_now / a.rel_pending));
+        a.cost[a.pending] += std::chrono::duration<double>(now - a.t_pending).count();
+        a.n[a.pending]++;
+    }
+    const int K = (int)a.cand.size();
+    int pick = -1;
+    for (int k = 0; k < K && pick < 0; k++)
+        if (a.n[k] < 2) pick = k;
+    if (pick < 0) {
+        a.rng ^= a.rng << 13;
+        a.rng ^= a.rng >> 7;
+        a.rng ^= a.rng << 17;
+        if (a.rng % 8 == 0) {
+            pick = (int)((a.rng >> 8) % K);
+        } else {
+            double best = -1.0;
+            for (int k = 0; k < K; k++) {
+                const double e = a.cost[k] > 0 ? a.gain[k] / a.cost[k] : 0.0;
+                if (e > best) {
+                    best = e;
+                    pick = k;
+                }
+            }
+        }
+    }
+    a.pending = pick;
+    a.rel_pending = rel_now;
+    a.t_pending = now;
+    a.uses++;
+    return a.cand[pick];
+}
+
 // Inner FP32 FGMRES on D_N (Sec. 5.3): low-accuracy FP32 sign, Wilson preconditioner.
 static ovl_status inner_solve(Ctx *c, const float *in, float *out) {
     ST(ensure_krylov<float>(c, c->kry_inner, c->p.restart_inner, true));
@@ -325,8 +377,10 @@ static ovl_status inner_solve(Ctx *c, const float *in, float *out) {
         const double t = relax_tol(c, eps, rel_now < 0 ? eps : rel_now, 1e-6, 1e-1);
         return c->sign32((const float4 *)a, (float4 *)o, t, 1);
     };
+    c->m0a.pending = -1;   // a new inner solve: nothing to credit from the previous one
     auto pc = [&](const float *a, float *o) -> ovl_status {
-        return wilson_solve<float>(c, c->kry_wil32, a, o, c->m0_prec, c->p.eps_prec);
+        const double m0 = c->p.m0_adapt ? m0_adapt_pick(c, c->fgmres_rel) : c->m0_prec;
+        return wilson_solve<float>(c, c->kry_wil32, a, o, m0, c->p.eps_prec);
     };
     KrylovResult r;
     ST(fgmres<float>(c, c->kry_inner, out, in, eps, c->p.max_inner, true, mv, &pc, &r, false));

@@ -163,6 +163,19 @@ struct Ctx {
     long ks_cycles = 0, ks_matvecs = 0;               // totals since creation
     // two-level multigrid for the Wilson solves (params.wilson_mg)
     MgData mg;
+    // On-the-fly choice of the Wilson preconditioner mass of the inner FGMRES (params.m0_adapt):
+    // candidate masses around m0^def, each scored by the residual reduction of the inner
+    // FGMRES iteration its preconditioner application served, per second of that iteration.
+    struct M0Adapt {
+        std::vector<double> cand, gain, cost;
+        std::vector<long> n;
+        int pending = -1;                    // candidate of the last application, not yet scored
+        double rel_pending = 0;              // relative residual before that application
+        std::chrono::steady_clock::time_point t_pending{};
+        uint64_t rng = 0x2545F4914F6CDD1Dull;
+        long uses = 0;
+    } m0a;
+    double fgmres_rel = -1;   // relative residual estimate of the FGMRES calling the preconditioner
     // batches of several right-hand sides sized by params.rhs_block alone, not by the free
     // device memory (set by the serving loop, which reserves that memory at admission, so
     // that a request's batching does not depend on what else is running)

@@ -136,3 +136,31 @@ def test_mg_arguments_rejected():
     with pytest.raises(ovl.OvlError):
         ovl.Overlap(U, dims, 1.0, 0.05, _mg_params((4, 4, 4, 4), 4, 1, 8, 0.1, wilson_mg=1,
                                                    precond=ovl.OVL_PREC_WILSON))
+
+
+def test_on_the_fly_preconditioner_mass():
+    """m0_adapt (Sec. 5.1: m0_prec changed from one preconditioned FGMRES iteration to the next):
+    the solve still matches dense LU, every candidate mass is tried, and the scores persist
+    across solves."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 1001)
+    rho = dense.rho_from_mu(0.05, -1.0)
+    DN, S, w = dense.overlap_dense(U, dims, rho, -1.0)
+    aw = np.abs(w)
+    b = synth.rhs_gaussian(dims, 2001)
+    p = ovl.params_default(lambda_min=0.98 * aw.min(), lambda_max=1.02 * aw.max(), precond=ovl.OVL_PREC_RECURSIVE,
+                           precision=ovl.OVL_MIXED_FP32, m0_adapt=1, eps_inner=1e-3)
+    op = ovl.Overlap(U, dims, 1.0, 0.05, p)
+    uses = []
+    for _ in range(3):
+        x = torch.zeros_like(dev(b))
+        st, stats = op.ovl_solve(x, dev(b), 1, 1e-10)
+        assert st == ovl.OVL_OK
+        assert rel2(x.cpu().numpy(), dense.overlap_solve_dense(DN, b)) < 1e-8
+        uses.append(op.m0_adapt_info()["uses"])
+    info = op.m0_adapt_info()
+    m0 = op.info()["m0_prec"]
+    assert np.allclose(info["cand"], [m0 * (1.5 - 0.25 * k) for k in range(5)])
+    assert uses[0] > 0 and uses[2] > uses[1] > uses[0]
+    assert sum(e > 0 for e in info["eff"]) >= 3 and info["best"] in info["cand"]
+    op.close()
