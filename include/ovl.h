@@ -160,8 +160,8 @@ typedef struct {
     double mg_coarse_tol;   /* a coarse solve stops early at this relative residual (default 0.1) */
     int m0_adapt;           /* 1: choose the Wilson preconditioner mass of the inner FGMRES (precond =
                                OVL_PREC_RECURSIVE, one right-hand side at a time) on the fly, from one
-                               FGMRES iteration to the next (Sec. 5.1): five candidates over
-                               [1.5 m0_prec, 0.5 m0_prec], each scored by the drop of the residual
+                               FGMRES iteration to the next (Sec. 5.1): five candidates evenly over
+                               [1.5 m0_prec, 0], each scored by the drop of the residual
                                estimate per second of the iteration it served; the scores persist in
                                the context across solves. 0 (default): always m0_prec */
 } ovl_params;

@@ -321,7 +321,8 @@ static double relax_tol(Ctx *c, double target, double rel_now, double lo, double
 // Wilson preconditioner mass for the next inner FGMRES iteration (params.m0_adapt), Sec. 5.1:
 // the paper observes that the best m0_prec is not known a priori and suggests approximating
 // it "on the fly" by changing it from one preconditioned FGMRES iteration to the next, without
-// a rule. Reading: five candidates spread over [1.5 m0_def, 0.5 m0_def]; the application made
+// a rule. Reading: five candidates spread evenly over [1.5 m0_def, 0] (the part of the paper's
+// scan range [-sigma~_min, 0] around m0_def; 0 included); the application made
 // with candidate i is credited, once the next iteration starts, with the drop of the FGMRES
 // residual estimate, -log(r_new / r_old), and with the wall time in between (its Wilson solve
 // and the D_N product of that iteration). Each candidate is tried twice, then the one with the
@@ -331,7 +332,7 @@ static double m0_adapt_pick(Ctx *c, double rel_now) {
     const auto now = std::chrono::steady_clock::now();
     if (a.cand.empty()) {
         const double m = c->m0_prec;
-        for (int k = 0; k < 5; k++) a.cand.push_back(m * (1.5 - 0.25 * k));
+        for (int k = 0; k < 5; k++) a.cand.push_back(m * (1.5 - 0.375 * k));
         a.gain.assign(5, 0.0);
         a.cost.assign(5, 0.0);
         a.n.assign(5, 0);

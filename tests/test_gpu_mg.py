@@ -160,7 +160,7 @@ def test_on_the_fly_preconditioner_mass():
         uses.append(op.m0_adapt_info()["uses"])
     info = op.m0_adapt_info()
     m0 = op.info()["m0_prec"]
-    assert np.allclose(info["cand"], [m0 * (1.5 - 0.25 * k) for k in range(5)])
+    assert np.allclose(info["cand"], [m0 * (1.5 - 0.375 * k) for k in range(5)])
     assert uses[0] > 0 and uses[2] > uses[1] > uses[0]
     assert sum(e > 0 for e in info["eff"]) >= 3 and info["best"] in info["cand"]
     op.close()
