@@ -2,11 +2,12 @@
 profilers (ncu). Nothing is timed here; the benchmark is bench.py.
 
     python -m paper_1410_7170_gb300.profile_run --what solve_mixed|solve_fp64|sign64|sign_ff|sign64_krylov|sap|dslash64|dslash32|dslash_ff
-        [--lattice 16x16x16x16] [--stout 3] [--stencil-tps 1] [--sap-tps 1] [--relax 0.3]
+        [--lattice 16x16x16x16] [--stout 3] [--stencil-tps 1] [--sap-tps 1] [--relax 0.3] [--m0-prec 0.0]
 
 The gauge field, right-hand side and solver settings are those of bench.py's 16^4
 workload (seeded links exp(i 0.5 H) smeared by 3 stout steps, rho = 1, mu = 0.01,
-one Gaussian right-hand side, tol 1e-8, relaxation factor 0.3). Under a profiler the autotuner's timings are
+one Gaussian right-hand side, tol 1e-8, relaxation factor 0.3, and for the mixed solve the
+Wilson preconditioner mass 0.0). Under a profiler the autotuner's timings are
 distorted, so --stencil-tps / --sap-tps fix the kernel variants (0 = autotune).
 """
 import argparse
@@ -34,6 +35,7 @@ def main():
     ap.add_argument("--stencil-tps", type=int, default=0)
     ap.add_argument("--sap-tps", type=int, default=0)
     ap.add_argument("--relax", type=float, default=0.3)
+    ap.add_argument("--m0-prec", type=float, default=0.0)
     a = ap.parse_args()
     build.build()
     dims = tuple(int(v) for v in a.lattice.split("x"))
@@ -41,7 +43,7 @@ def main():
     b = torch.from_numpy(synth.rhs_gaussian(dims, 2002)).cuda()
     tune = dict(stencil_tps=a.stencil_tps, sap_tps=a.sap_tps, relax_factor=a.relax)
     if a.what == "solve_mixed":
-        p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, **tune)
+        p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, m0_prec=a.m0_prec, **tune)
     elif a.what == "solve_fp64":
         p = ovl.params_default(precond=ovl.OVL_PREC_WILSON, precision=ovl.OVL_FP64, prec_max_iter=4, **tune)
     elif a.what == "sign64_krylov":
