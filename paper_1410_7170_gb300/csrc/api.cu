@@ -299,7 +299,8 @@ ovl_status Ctx::ms_setup(MsState *d_state, double tol, int *n_out) {
 // device logs how many shifts each iteration updated, so per-kernel durations and
 // algorithmic bytes come from the same launches that do the work.
 template <typename Iter>
-ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes, Iter iter_fn, int *iters_out) {
+ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes, bool fused, Iter iter_fn,
+                       int *iters_out) {
     Ctx *c = this;
     const int chunk = std::min(p.check_every, kMaxChunk);
     const int sample = chunk / 2;   // the iteration of every chunk whose kernels are timed
@@ -349,10 +350,12 @@ ovl_status Ctx::ms_run(MsState *d_state, int which, int slot, double shift_bytes
             const double V = (double)g.V;
             ProfAcc &pa = pacc[which];
             // algorithmic reals per site: Q p: p, 4 links x 12, t; residual: t, links, p, r in/out;
-            // shifts: r, y in/out, each updated p_l in/out
-            const double qb = 96.0 * V * rbytes, rb = 144.0 * V * rbytes;
+            // shifts: r, y in/out, each updated p_l in/out. Fused form: the residual kernel also
+            // moves y in/out and the p_l (l >= 1), the third kernel r, p_0 in/out.
+            const double qb = 96.0 * V * rbytes;
             for (int k = 0; k < ran; k++) {
-                const double sb = (72.0 * rbytes + shift_bytes * h_hist[k]) * V;
+                const double rb = fused ? (192.0 * rbytes + shift_bytes * (h_hist[k] - 1)) * V : 144.0 * V * rbytes;
+                const double sb = fused ? 72.0 * rbytes * V : (72.0 * rbytes + shift_bytes * h_hist[k]) * V;
                 pa.n++;
                 pa.q_bytes += qb;
                 pa.r_bytes += rb;
@@ -410,7 +413,7 @@ ovl_status Ctx::sign64(const double2 *b, double2 *out, double tol, int mode) {
     int iters = 0;
     auto fn = [&](cudaEvent_t *e, unsigned f) { return ms_iter_f64(g, U64, m0_ker, ms64_state, ms64, rs, stream, e, f); };
     // at the iteration cap the output is still formed from the last iterate (status ENOCONV)
-    const ovl_status ms = ms_run(ms64_state, 0, 0, 48.0 * 8.0, fn, &iters);
+    const ovl_status ms = ms_run(ms64_state, 0, 0, 48.0 * 8.0, false, fn, &iters);
     if (ms != OVL_OK && ms != OVL_ENOCONV) return ms;
     stat_ms64 += iters;
     const double sc = zs_d0[n - 1] / lam_min;
@@ -443,7 +446,7 @@ ovl_status Ctx::sign_ff(const double2 *b, double2 *out, double tol, int mode) {
     CK(ms_init_ff(g, n, msff_state, msff, msff.t, rs, stream));
     int iters = 0;
     auto fn = [&](cudaEvent_t *e, unsigned f) { return ms_iter_ff(g, Uff, m0_ker, msff_state, msff, rs, stream, e, f); };
-    const ovl_status ms = ms_run(msff_state, 2, 5, 48.0 * 8.0, fn, &iters);
+    const ovl_status ms = ms_run(msff_state, 2, 5, 48.0 * 8.0, false, fn, &iters);
     if (ms != OVL_OK && ms != OVL_ENOCONV) return ms;
     stat_msff += iters;
     const double sc = zs_d0[n - 1] / lam_min;
@@ -538,7 +541,7 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode, int s
         auto fn = [&](cudaEvent_t *e, unsigned f) {
             return ms_iter_half(g, U32, (float)m0_ker, msh_state, msh, rs, bf, stream, e, f);
         };
-        ms = ms_run(msh_state, 1, bf ? 6 : 2, bf ? 96.0 : 104.0, fn, &iters);
+        ms = ms_run(msh_state, 1, bf ? 6 : 2, bf ? 96.0 : 104.0, false, fn, &iters);
         if (ms != OVL_OK && ms != OVL_ENOCONV) return ms;
         y = msh.y;
     } else {
@@ -548,7 +551,7 @@ ovl_status Ctx::sign32(const float4 *b, float4 *out, double tol, int mode, int s
         auto fn = [&](cudaEvent_t *e, unsigned f) {
             return ms_iter_f32(g, U32, (float)m0_ker, ms32_state, ms32, rs, stream, e, f);
         };
-        ms = ms_run(ms32_state, 1, 1, 48.0 * 4.0, fn, &iters);
+        ms = ms_run(ms32_state, 1, 1, 48.0 * 4.0, g.tps32 != 4, fn, &iters);
         if (ms != OVL_OK && ms != OVL_ENOCONV) return ms;
         y = ms32.y;
     }
@@ -776,12 +779,13 @@ ovl_status Ctx::ensure_ms32() {
     if (ms32.p) return OVL_OK;
     const long words = (long)g.V * 6;    // float4 per vector
     void *buf;
-    ST(alloc(&buf, (size_t)words * sizeof(float4) * (npole + 3)));
+    ST(alloc(&buf, (size_t)words * sizeof(float4) * (npole + 4)));
     float4 *b4 = (float4 *)buf;
     ms32.r = b4;
     ms32.t = b4 + words;
     ms32.y = b4 + 2 * words;
     ms32.p = b4 + 3 * words;
+    ms32.r2 = b4 + (3 + npole) * words;
     ms32.stride = words;
     return OVL_OK;
 }

@@ -173,6 +173,7 @@ struct MsVectors {
     ST *t;       // Q p_0
     ST *y;       // accumulated rational function argument
     ST *p;       // n search directions, p[l] at p + l * stride
+    ST *r2;      // FP32 only: second residual buffer of the fused iteration (r_k in r for even k, r2 odd)
     long stride; // elements of ST per vector
 };
 

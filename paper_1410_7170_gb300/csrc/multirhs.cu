@@ -2,8 +2,9 @@
 // multishift CG that runs one independent Zolotarev sign evaluation per right-hand side
 // in lock-step.
 //
-// Thread blocks are 32 sites x nr right-hand sides (threadIdx.x = site, threadIdx.y =
-// right-hand side). The nr threads of one site need the same eight links; running them
+// The FP32 multi-RHS stencil loops over the right-hand sides inside each thread (see
+// k_wilson_mrhs_pairs). The FP64 stencil and the batched multishift kernels use thread blocks
+// of 32 sites x nr right-hand sides (threadIdx.x = site, threadIdx.y = right-hand side). The nr threads of one site need the same eight links; running them
 // in one block makes the repeats hit L1, so DRAM sees each link once per block of
 // right-hand sides: per site and right-hand side the stencil moves 48 / nr link reals
 // plus 48 spinor reals instead of 96. Each warp holds one right-hand side, so warp sums
@@ -48,41 +49,46 @@ __global__ void __launch_bounds__(384) k_wilson_mrhs(Geom g, const LT *__restric
     store_spinor<R>(out + rhs * stride, g.Vh, p, i, res);
 }
 
-// FP32 variant with two right-hand sides per thread: thread (x, y) handles right-hand sides
-// 2y and 2y + 1 of site x and applies every link it loads to both (an odd last one runs
-// alone). Per site and right-hand side the L1/L2 link traffic halves again, from 48 reals
-// to 24 for every two right-hand sides.
-__global__ void __launch_bounds__(kTile * 6) k_wilson_mrhs2(Geom g, const float4 *__restrict__ U,
-                                                          const float4 *__restrict__ in, float4 *__restrict__ out,
-                                                          long stride, int nrhs, float m4, int g5, float a,
-                                                          const float4 *z, float b) {
-    const int r0 = 2 * (int)threadIdx.y;
-    const int t = tile_site(blockIdx.x);
-    if (r0 >= nrhs || t >= g.V) return;
-    const bool two = r0 + 1 < nrhs;
+// FP32 multi-RHS stencil: each thread owns one site in the single-RHS order (blocks of up to 256
+// consecutive sites, both parities interleaved, so most x3 and x2 neighbours of a block hit L1)
+// and loops over the right-hand sides two at a time, applying every link it loads to both
+// (wilson_hop2). A block of 32 sites x nr right-hand sides (k_wilson_mrhs) shares the links
+// across right-hand sides too, but its blocks span one x3 row, so the x2 neighbours miss L1 and
+// the spinor gathers that bound this stencil grow; measured per right-hand side at 12 of them it
+// ran 1.16x the single-RHS time at 64x32^3, this loop 0.95x (32^4: 0.88x, 16^4: 0.52x).
+__global__ void __launch_bounds__(kBlock, 2) k_wilson_mrhs_pairs(Geom g, const float4 *__restrict__ U,
+                                                               const float4 *__restrict__ in, float4 *__restrict__ out,
+                                                               long stride, int nrhs, float m4, int g5, float a,
+                                                               const float4 *z, float b, int spb) {
+    const int t = blockIdx.x * spb + threadIdx.x;
+    if (threadIdx.x >= spb || t >= g.V) return;
     int p, i;
     site_of_thread(t, p, i);
-    const float4 *x0 = in + r0 * stride, *x1 = two ? x0 + stride : x0;
-    cpx<float> hop[2][12];
-    wilson_hop2<float>(g, U, x0, x1, p, i, hop[0], hop[1]);
+#pragma unroll 1
+    for (int r = 0; r < nrhs; r += 2) {
+        const bool two = r + 1 < nrhs;
+        const float4 *x0 = in + r * stride, *x1 = two ? x0 + stride : x0;
+        cpx<float> hop[2][12];
+        wilson_hop2<float>(g, U, x0, x1, p, i, hop[0], hop[1]);
 #pragma unroll
-    for (int f = 0; f < 2; f++) {
-        if (f == 1 && !two) break;
-        const int rhs = r0 + f;
-        cpx<float> own[12], res[12];
-        load_spinor<float>(in + rhs * stride, g.Vh, p, i, own);
-        wilson_combine<float>(m4, own, hop[f], res);
-        if (g5) apply_g5(res);
-        if (z) {
-            cpx<float> zz[12];
-            load_spinor<float>(z + rhs * stride, g.Vh, p, i, zz);
+        for (int f = 0; f < 2; f++) {
+            if (f == 1 && !two) break;
+            const int rhs = r + f;
+            cpx<float> own[12], res[12];
+            load_spinor<float>(in + rhs * stride, g.Vh, p, i, own);
+            wilson_combine<float>(m4, own, hop[f], res);
+            if (g5) apply_g5(res);
+            if (z) {
+                cpx<float> zz[12];
+                load_spinor<float>(z + rhs * stride, g.Vh, p, i, zz);
 #pragma unroll
-            for (int c = 0; c < 12; c++) res[c] = a * res[c] + b * zz[c];
-        } else {
+                for (int c = 0; c < 12; c++) res[c] = a * res[c] + b * zz[c];
+            } else {
 #pragma unroll
-            for (int c = 0; c < 12; c++) res[c] = a * res[c];
+                for (int c = 0; c < 12; c++) res[c] = a * res[c];
+            }
+            store_spinor<float>(out + rhs * stride, g.Vh, p, i, res);
         }
-        store_spinor<float>(out + rhs * stride, g.Vh, p, i, res);
     }
 }
 
@@ -412,10 +418,11 @@ cudaError_t wilson_batch_f64(const Geom &g, const double2 *U, const double2 *in,
 }
 cudaError_t wilson_batch_f32(const Geom &g, const float4 *U, const float4 *in, float4 *out, long stride, int nrhs,
                              float m0, int g5, float a, const float4 *z, float b, cudaStream_t st) {
-    if (nrhs > 1)
-        k_wilson_mrhs2<<<dim3((g.V + kTile - 1) / kTile, 1), dim3(kTile, (nrhs + 1) / 2), 0, st>>>(
-            g, U, in, out, stride, nrhs, m0 + 4.f, g5, a, z, b);
-    else
+    if (nrhs > 1) {
+        const LaunchShape ls = balanced_shape(g.V, g.nsm, 2, 1 << 30);
+        k_wilson_mrhs_pairs<<<ls.grid, ls.block, 0, st>>>(g, U, in, out, stride, nrhs, m0 + 4.f, g5, a, z, b,
+                                                          ls.spb);
+    } else
         k_wilson_mrhs<float, float4, float4><<<dim3((g.V + kTile - 1) / kTile, 1), dim3(kTile, nrhs), 0, st>>>(
             g, U, in, out, stride, nrhs, m0 + 4.f, g5, a, z, b);
     count_launches(1);

@@ -24,6 +24,23 @@
 //   ms_q:      t = Q p_0 (stencil with gamma5),       reduce ||t||^2 -> alpha
 //   ms_r:      r -= alpha (gamma5 D_W t + sigma_0 p_0), reduce ||r||^2 -> beta, shift scalars
 //   ms_shifts: y += sum_l w~_l p~_l ; p~_l = r + b~_l p~_l   (pure streaming)
+// The FP32 iteration with one thread per site instead updates the shifted directions one
+// iteration late, inside ms_r, where their memory traffic overlaps the stencil's waits:
+//   ms_q (+ zeta):  t = Q p_0, alpha_k, and zeta_{k+1} of every shift (it needs only alpha_k
+//                   and the previous iteration's scalars)
+//   ms_rf:          r_{k+1} = r_k - alpha_k (Q t + sigma_0 p_0); at the same site
+//                   p~_l(k) = r_k + b^l_{k-1} p~_l(k-1) (l >= 1) and y += w_l alpha^l_k p~_l(k)
+//                   (l >= 0); reduce ||r_{k+1}||^2 -> beta_k, b^l_k, dropped shifts
+//   ms_p0:          p_0 = r_{k+1} + beta_k p_0 (the stencil of the next ms_q reads it)
+// r alternates between two buffers (r_k in r for even k, in r2 for odd k), so the shift
+// updates of ms_rf can read r_k at any point of the kernel.
+// The arithmetic of each update is the same as in the three-kernel form; only p~_l(k) is
+// formed in iteration k instead of at the end of iteration k-1. In ms_rf odd warps stream
+// their shift updates before their stencil and even warps after it, so that on every SM
+// some warps stream while the others gather. Measured at 16^4 the FP32 iteration falls from
+// 49 to 47 us; the float-float one rose from 147 to 171 us (its shift updates are float-float
+// arithmetic on a kernel already bound by arithmetic), so FP64 and float-float keep the
+// three-kernel form.
 // (p_0, Q^2 p_0) = ||Q p_0||^2 because Q is Hermitian (Eq. gamma_5_symmetry).
 // After convergence (state->done) every kernel returns at once, so a fixed number
 // of iterations can be queued or captured in a CUDA graph without host round trips.
@@ -115,8 +132,84 @@ struct ShiftFin {
     }
 };
 
-// t = gamma5 D_W(m) p0 ; reduce ||t||^2
-template <typename R, typename LT, typename ST>
+// Fused form, end of ms_q (one warp, lane j handles shifts j, j+32): alpha_k, then for every
+// active shift zeta_{k+1} and alpha^l_k = alpha_k zeta_{k+1} (the coefficient of this
+// iteration's y update); the base shift has zeta = 1.
+struct AlphaFinZ {
+    MsState *s;
+    __device__ void operator()(const double *v, int lane) const {
+        const double pAp = v[0] + s->sigma[0] * s->pp;
+        const double a = s->rr / pAp;
+        if (!(pAp > 0.0) || !isfinite(a)) {
+            if (lane == 0) {
+                s->status = 1;
+                s->done = 1;
+            }
+            return;
+        }
+        const double ap = s->alpha_prev, bp = s->beta_prev;
+        for (int l = lane; l < s->n; l += 32) {
+            if (!s->active[l]) continue;
+            double zn = 1.0;
+            if (l > 0) {
+                const double z = s->zeta[l], zp = s->zeta_prev[l];
+                const double den = a * bp * (zp - z) + zp * ap * (1.0 + (s->sigma[l] - s->sigma[0]) * a);
+                zn = (den != 0.0) ? z * zp * ap / den : 0.0;
+            }
+            s->alpha_l[l] = a * zn;
+            s->zeta_prev[l] = s->zeta[l];
+            s->zeta[l] = zn;
+        }
+        __syncwarp();
+        if (lane == 0) s->alpha = a;
+    }
+};
+
+// Fused form, end of ms_rf: beta_k, the next iteration's direction coefficients
+// b^l_k = beta_k zeta_{k+1} / zeta_k, and the drop rule on the residual bound after this
+// iteration's update (whose y contribution ms_rf has already added, so a dropped shift
+// retires at once). The base direction stays while any shift is open.
+struct ShiftFinL {
+    MsState *s;
+    __device__ void operator()(const double *v, int lane) const {
+        const double rr_new = v[0];
+        const double beta = rr_new / s->rr;
+        if (!isfinite(beta)) {
+            if (lane == 0) {
+                s->status = 1;
+                s->done = 1;
+            }
+            return;
+        }
+        const double rnorm = sqrt(rr_new), tolb = s->tol * sqrt(s->bb);
+        int any = 0, nupd = 0;
+        for (int l = lane; l < s->n; l += 32) {
+            if (!s->active[l]) continue;
+            nupd++;
+            const double z = s->zeta[l], zp = s->zeta_prev[l];
+            s->beta_l[l] = beta * ((zp != 0.0) ? z / zp : 0.0);
+            const bool conv = s->crit[l] * fabs(z) * rnorm <= tolb;
+            if (!conv) any = 1;
+            else if (l > 0) s->active[l] = 0;
+        }
+        any = __any_sync(0xffffffffu, any);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nupd += __shfl_down_sync(0xffffffffu, nupd, off);
+        __syncwarp();
+        if (lane == 0) {
+            if (s->hist && s->iter < s->hist_cap) s->hist[s->iter] = nupd;
+            s->alpha_prev = s->alpha;
+            s->beta_prev = beta;
+            s->pp = rr_new + beta * beta * s->pp;
+            s->rr = rr_new;
+            s->iter += 1;
+            if (!any) s->done = 1;
+        }
+    }
+};
+
+// t = gamma5 D_W(m) p0 ; reduce ||t||^2 (Fused: also the shifts' zeta_{k+1}, AlphaFinZ)
+template <typename R, typename LT, typename ST, bool Fused>
 __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, const LT *__restrict__ U, R m4, MsState *s,
                                                  const ST *__restrict__ p0, ST *__restrict__ t, RedScratch rs,
                                                  int spb) {
@@ -137,7 +230,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_q(Geom g, co
         for (int c = 0; c < 12; c++) a0 += norm2(res[c]);
         v[0] += a0;
     }
-    grid_reduce<1>(v, rs, AlphaFin{s});
+    if constexpr (Fused) grid_reduce_warp<1>(v, rs, AlphaFinZ{s});
+    else grid_reduce<1>(v, rs, AlphaFin{s});
 }
 
 // r -= alpha (gamma5 D_W(m) t + sigma0 p0) ; reduce ||r||^2 ; shift scalars
@@ -337,6 +431,129 @@ __global__ void __launch_bounds__(kBlock) k_ms_shifts(MsState *s, const ST *__re
     }
 }
 
+// Lagged shift updates at site (p, i), word by word: y += wa0 p_0 ; for the active shifts
+// l >= 1: p~_l = r_k + b_l p~_l, y += wa_l p~_l.
+template <typename ST, typename R>
+__device__ __forceinline__ void shift_updates_site(const ST *__restrict__ rk, ST *__restrict__ P, long stride,
+                                                   ST *__restrict__ y, int Vh, int p, int i, int na, const int *sidx,
+                                                   const R *sw, const R *sb, R sw0) {
+    constexpr int N = Word<ST>::N, W = 24 / N;
+    constexpr int kB = 2;   // shifts whose words are loaded together
+#pragma unroll 2
+    for (int w = 0; w < W; w++) {
+        const size_t off = ((size_t)p * W + w) * Vh + i;
+        R rw[N], yv[N], p0[N];
+        Word<ST>::get(rk[off], rw);
+        Word<ST>::get(y[off], yv);
+        Word<ST>::get(P[off], p0);
+#pragma unroll
+        for (int e = 0; e < N; e++) yv[e] = fma_r(sw0, p0[e], yv[e]);
+        for (int a0 = 0; a0 < na; a0 += kB) {
+            ST wv[kB];
+#pragma unroll
+            for (int u = 0; u < kB; u++)
+                if (a0 + u < na) wv[u] = P[(long)sidx[a0 + u] * stride + off];
+#pragma unroll
+            for (int u = 0; u < kB; u++) {
+                if (a0 + u >= na) break;
+                R pv[N];
+                Word<ST>::get(wv[u], pv);
+                const R wl = sw[a0 + u], bl = sb[a0 + u];
+#pragma unroll
+                for (int e = 0; e < N; e++) {
+                    pv[e] = fma_r(bl, pv[e], rw[e]);
+                    yv[e] = fma_r(wl, pv[e], yv[e]);
+                }
+                P[(long)sidx[a0 + u] * stride + off] = Word<ST>::put(pv);
+            }
+        }
+        y[off] = Word<ST>::put(yv);
+    }
+}
+
+// Fused residual kernel (one thread per site): r_{k+1} = r_k - alpha (gamma5 D_W t + sigma_0 p_0)
+// and the lagged shift updates of the same site; reduce ||r_{k+1}||^2 -> ShiftFinL.
+// r_k is read from buf[k & 1] and r_{k+1} written to buf[(k + 1) & 1] (buf = {r, r2}), so the
+// shift updates can read r_k after the stencil has produced r_{k+1}.
+template <typename R, typename LT, typename ST>
+__global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_rf(Geom g, const LT *__restrict__ U, R m4,
+                                                                     MsState *s, const ST *__restrict__ t, ST *P,
+                                                                     long stride, ST *r, ST *r2, ST *y,
+                                                                     RedScratch rs, int spb) {
+    __shared__ R sw[kMaxPoles], sb[kMaxPoles];
+    __shared__ int sidx[kMaxPoles];
+    __shared__ int sact, sdone;
+    __shared__ R sw0;
+    __shared__ int sodd;
+    if (threadIdx.x == 0) {
+        sdone = s->done;
+        sodd = s->iter & 1;
+        int na = 0;
+        if (!sdone)
+            for (int l = 1; l < s->n; l++)
+                if (s->active[l]) {
+                    sidx[na] = l;
+                    sw[na] = R(s->w[l] * s->alpha_l[l]);
+                    sb[na] = R(s->beta_l[l]);
+                    na++;
+                }
+        sact = na;
+        sw0 = R(s->w[0] * s->alpha_l[0]);
+    }
+    __syncthreads();
+    if (sdone) return;
+    const int na = sact;
+    const ST *rin = sodd ? r2 : r;
+    ST *rout = sodd ? r : r2;
+    const R alpha = R(s->alpha), sig0 = R(s->sigma[0]), w0 = sw0;
+    R v[1] = {R(0)};
+    const bool shifts_first = (threadIdx.x >> 5) & 1;
+    const bool lane_has_sites = threadIdx.x < spb;
+    for (int k = blockIdx.x * spb + threadIdx.x; lane_has_sites && k < g.V; k += gridDim.x * spb) {
+        int p, i;
+        site_of_thread(k, p, i);
+        if (shifts_first) shift_updates_site<ST, R>(rin, P, stride, y, g.Vh, p, i, na, sidx, sw, sb, w0);
+        {
+            cpx<R> hop[12], own[12], res[12], pp[12], rv[12];
+            wilson_hop<R>(g, U, t, p, i, hop);
+            load_spinor<R>(t, g.Vh, p, i, own);
+            wilson_combine<R>(m4, own, hop, res);
+            apply_g5(res);
+            load_spinor<R>(P, g.Vh, p, i, pp);
+            load_spinor<R>(rin, g.Vh, p, i, rv);
+            R a0 = R(0);
+#pragma unroll
+            for (int c = 0; c < 12; c++) {
+                rv[c] = rv[c] - alpha * (res[c] + sig0 * pp[c]);
+                a0 += norm2(rv[c]);
+            }
+            v[0] += a0;
+            store_spinor<R>(rout, g.Vh, p, i, rv);
+        }
+        if (!shifts_first) shift_updates_site<ST, R>(rin, P, stride, y, g.Vh, p, i, na, sidx, sw, sb, w0);
+    }
+    grid_reduce_warp<1>(v, rs, ShiftFinL{s});
+}
+
+// p_0 = r_{k+1} + beta_k p_0 (fused form; nw words)
+template <typename ST>
+__global__ void __launch_bounds__(kBlock) k_ms_p0(const MsState *s, const ST *__restrict__ rb0,
+                                                  const ST *__restrict__ rb1, ST *__restrict__ P0, long nw) {
+    if (s->done) return;
+    const ST *__restrict__ r = (s->iter & 1) ? rb1 : rb0;
+    using A = typename Word<ST>::A;
+    constexpr int N = Word<ST>::N;
+    const A b = A(s->beta_prev);
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (long)gridDim.x * blockDim.x) {
+        A rv[N], pv[N];
+        Word<ST>::get(r[k], rv);
+        Word<ST>::get(P0[k], pv);
+#pragma unroll
+        for (int e = 0; e < N; e++) pv[e] = fma_r(b, pv[e], rv[e]);
+        P0[k] = Word<ST>::put(pv);
+    }
+}
+
 struct InitFin {
     MsState *s;
     __device__ void operator()(const double *v) const {
@@ -473,13 +690,22 @@ cudaError_t ms_iter_t(const Geom &g, const LT *U, R m0, MsState *s, MsVectors<ST
     const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<R>::value, kMaxRedBlocks);
     cudaError_t e;
     if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
-    if (tps == 4) k_ms_q4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
-    else k_ms_q<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs, ls.spb);
-    if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
-    if (tps == 4) k_ms_r4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
-    else k_ms_r<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs, ls.spb);
-    if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
-    k_ms_shifts<ST><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.y, v.p, v.stride, v.stride, rs.counter);
+    // the fused form pays where the stencil waits on memory (FP32); the FP64 and float-float
+    // stencils are bound by arithmetic that the shift updates would add to
+    if (tps == 4 || sizeof(R) != 4) {   // three-kernel form
+        k_ms_q4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
+        if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
+        k_ms_r4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
+        if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
+        k_ms_shifts<ST><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.y, v.p, v.stride, v.stride, rs.counter);
+    } else {          // fused form
+        k_ms_q<R, LT, ST, true><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs, ls.spb);
+        if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
+        k_ms_rf<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.stride, v.r, v.r2, v.y,
+                                                         rs, ls.spb);
+        if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
+        k_ms_p0<ST><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.r2, v.p, v.stride);
+    }
     if (ev && (e = cudaEventRecordWithFlags(ev[3], st, ev_flags)) != cudaSuccess) return e;
     count_launches(3);
     return cudaGetLastError();
@@ -522,7 +748,7 @@ cudaError_t ms_iter_ff(const Geom &g, const ffw *U, double m0, MsState *s, MsVec
     const ff m4(m0 + 4.0);
     cudaError_t e;
     if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
-    k_ms_q<ff, ffw, ffw><<<ls.grid, ls.block, 0, st>>>(g, U, m4, s, v.p, v.t, rs, ls.spb);
+    k_ms_q<ff, ffw, ffw, false><<<ls.grid, ls.block, 0, st>>>(g, U, m4, s, v.p, v.t, rs, ls.spb);
     if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
     k_ms_r<ff, ffw, ffw><<<ls.grid, ls.block, 0, st>>>(g, U, m4, s, v.t, v.p, v.r, rs, ls.spb);
     if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
@@ -547,7 +773,7 @@ cudaError_t ms_iter_half(const Geom &g, const float4 *U, float m0, MsState *s, M
     const LaunchShape ls = balanced_shape(g.V, g.nsm, MinBlocks<float>::value, kMaxRedBlocks);
     cudaError_t e;
     if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
-    k_ms_q<float, float4, float4><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + 4.f, s, v.p0, v.t, rs, ls.spb);
+    k_ms_q<float, float4, float4, false><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + 4.f, s, v.p0, v.t, rs, ls.spb);
     if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
     k_ms_r<float, float4, float4><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + 4.f, s, v.t, v.p0, v.r, rs, ls.spb);
     if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;

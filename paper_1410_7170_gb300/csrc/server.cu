@@ -95,9 +95,10 @@ size_t estimate_bytes(const ovl_request &r, const ovl_params &p) {
     const double v64 = 24.0 * V * 8.0, v32 = 24.0 * V * 4.0;
     double b = V * 4 * (9 * 16 + 3 * 16);                 // links: FP64 18 reals + FP32 12 reals
     b += 3 * v64 + 6 * v32;                               // staging, Lanczos / tuning vectors
-    b += (p.n_poles + 3) * v64;                           // FP64 multishift
+    b += (p.n_poles + 3) * v64;                           // FP64 (or float-float) multishift
     const bool mixed = p.precision != OVL_FP64 || p.precond == OVL_PREC_RECURSIVE;
-    if (mixed) b += (p.n_poles + 3) * v32;                 // FP32 multishift
+    if (mixed) b += (p.n_poles + 4) * v32;                 // FP32 multishift
+    if (mixed && p.ff_outer) b += V * 4 * 9 * 16;          // float-float links
     if (p.sign_method == OVL_SIGN_KRYLOV) b += (p.krylov_m + p.krylov_keep + 3) * v64;   // Krylov sign basis
     if (p.n_deflate > 0) {
         // eigenvectors xi, gamma5 xi (FP64 and FP32) and scratch, plus the eigensolver's basis

@@ -204,7 +204,8 @@ struct Ctx {
     // which: instrumentation class (0 FP64, 1 FP32/FP16); slot: CUDA-graph slot;
     // shift_bytes: algorithmic bytes per site of one shift update (read + write of p_l)
     template <typename Iter>
-    ovl_status ms_run(MsState *d_state, int which, int slot, double shift_bytes, Iter iter_fn, int *iters_out);
+    ovl_status ms_run(MsState *d_state, int which, int slot, double shift_bytes, bool fused, Iter iter_fn,
+                      int *iters_out);
     ovl_status sign64(const double2 *b, double2 *out, double tol, int mode);
     // store: -1 = from params.precision, 0 = FP32, 1 = FP16-stored, 2 = BF16-stored directions
     ovl_status sign32(const float4 *b, float4 *out, double tol, int mode, int store = -1);
