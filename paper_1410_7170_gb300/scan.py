@@ -4,13 +4,17 @@ relaxation factor of the sign accuracy (Sec. 5.2, Table 2 uses 1e-2).
 
     python -m paper_1410_7170_gb300.scan [--lattice 16x16x16x16] [--mu 0.01]
         [--m0 -0.6:0.0:0.05] [--relax 0.01,0.03,0.1,0.3] [--adapt] [--reps 3]
+        [--set eps_inner=0.01,0.03 --set sap_mr_iters=4,6 ...]
 
 Each point is a full solve (outer FP64 FGMRES, recursive inner FP32 FGMRES, Wilson
 preconditioner) of the seeded workload (links exp(i 0.5 H) smeared by 3 stout steps, one
 Gaussian right-hand side, tol 1e-8), timed as the fastest of --reps solves after one
 warm-up solve. One JSON line per point: the parameters, seconds per solve, outer, inner and
 Wilson iterations, multishift iterations and the true residual. With --adapt a last line
-gives the on-the-fly mass choice (params.m0_adapt) on the same workload.
+gives the on-the-fly mass choice (params.m0_adapt) on the same workload. Each --set adds an
+ovl_params field and its values to the grid (the inner FGMRES reduction eps_inner of Table 3,
+the Wilson solve's eps_prec, prec_max_iter and Schwarz parameters of Sec. 5.1); the points are
+the product of all lists.
 """
 import argparse
 import json
@@ -24,6 +28,8 @@ if ROOT not in sys.path:
 
 
 def _range(spec):
+    if ":" not in spec:
+        return [float(v) for v in spec.split(",")]
     a, b, s = (float(v) for v in spec.split(":"))
     out, v = [], a
     while v <= b + 1e-12:
@@ -42,11 +48,17 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", default="16x16x16x16")
     ap.add_argument("--mu", type=float, default=0.01)
-    ap.add_argument("--m0", default="", help="start:stop:step of m0_prec (empty: m0^def only)")
+    ap.add_argument("--m0", default="", help="start:stop:step or a list of m0_prec (empty: m0^def only)")
     ap.add_argument("--relax", default="0.01", help="comma-separated relaxation factors")
     ap.add_argument("--adapt", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--set", action="append", default=[], help="field=v1,v2,... (repeatable)")
     a = ap.parse_args(argv)
+    grid = [{}]
+    for spec in a.set:
+        key, vals = spec.split("=", 1)
+        parsed = [int(v) if v.lstrip("-").isdigit() else float(v) for v in vals.split(",")]
+        grid = [dict(g, **{key: v}) for g in grid for v in parsed]
     build.build()
     dims = tuple(int(v) for v in a.lattice.split("x"))
     U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1002, stout_steps=3, device="cuda")).cuda()
@@ -74,15 +86,16 @@ def main(argv=None):
 
     for r in relaxes:
         for m in masses:
-            kw = {"relax_factor": r}
-            if m == m:   # not NaN
-                kw["m0_prec"] = m
-            s, st, info, _ = run(**kw)
-            print(json.dumps({"m0_prec": info["m0_prec"], "relax_factor": r, "s_per_solve": s,
-                              "outer": st["outer_iters"], "inner": st["inner_iters"], "wilson": st["prec_iters"],
-                              "ms_iters_tight": st["ms_iters_fp64"] + st["ms_iters_ff"],
-                              "ms_iters_low": st["ms_iters_low"], "true_rel_resid": st["true_rel_resid"]}),
-                  flush=True)
+            for extra in grid:
+                kw = {"relax_factor": r, **extra}
+                if m == m:   # not NaN
+                    kw["m0_prec"] = m
+                s, st, info, _ = run(**kw)
+                print(json.dumps({"m0_prec": info["m0_prec"], "relax_factor": r, **extra, "s_per_solve": s,
+                                  "outer": st["outer_iters"], "inner": st["inner_iters"], "wilson": st["prec_iters"],
+                                  "ms_iters_tight": st["ms_iters_fp64"] + st["ms_iters_ff"],
+                                  "ms_iters_low": st["ms_iters_low"], "true_rel_resid": st["true_rel_resid"]}),
+                      flush=True)
     if a.adapt:
         s, st, info, extra = run(relax_factor=relaxes[0], m0_adapt=1)
         print(json.dumps({"m0_adapt": extra, "m0_def": info["m0_prec"], "relax_factor": relaxes[0],
