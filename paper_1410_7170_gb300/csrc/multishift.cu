@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) k_ms_r4(Geom g, c
             C::template load<R>(t, g.Vh, p, i, j, own);
             C::template load<R>(p0, g.Vh, p, i, j, pp);
             C::template load<R>(r, g.Vh, p, i, j, rv);
-#pragma unroll
             R a0 = 0;
+#pragma unroll
             for (int e = 0; e < C::CPC; e++) {
                 const int cix = j * C::CPC + e;
                 cpx<R> res = m4 * own[e] + acc[cix];
@@ -692,10 +692,12 @@ cudaError_t ms_iter_t(const Geom &g, const LT *U, R m0, MsState *s, MsVectors<ST
     if (ev && (e = cudaEventRecordWithFlags(ev[0], st, ev_flags)) != cudaSuccess) return e;
     // the fused form pays where the stencil waits on memory (FP32); the FP64 and float-float
     // stencils are bound by arithmetic that the shift updates would add to
-    if (tps == 4 || sizeof(R) != 4) {   // three-kernel form
-        k_ms_q4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
+    if (tps == 4 || sizeof(R) != 4) {   // three-kernel form (4 or 1 threads per site)
+        if (tps == 4) k_ms_q4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs);
+        else k_ms_q<R, LT, ST, false><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.p, v.t, rs, ls.spb);
         if (ev && (e = cudaEventRecordWithFlags(ev[1], st, ev_flags)) != cudaSuccess) return e;
-        k_ms_r4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
+        if (tps == 4) k_ms_r4<R, LT, ST><<<gs, kBlock, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs);
+        else k_ms_r<R, LT, ST><<<ls.grid, ls.block, 0, st>>>(g, U, m0 + (R)4, s, v.t, v.p, v.r, rs, ls.spb);
         if (ev && (e = cudaEventRecordWithFlags(ev[2], st, ev_flags)) != cudaSuccess) return e;
         k_ms_shifts<ST><<<stream_grid(v.stride), kBlock, 0, st>>>(s, v.r, v.y, v.p, v.stride, v.stride, rs.counter);
     } else {          // fused form
