@@ -164,6 +164,11 @@ typedef struct {
                                [1.5 m0_prec, 0], each scored by the drop of the residual
                                estimate per second of the iteration it served; the scores persist in
                                the context across solves. 0 (default): always m0_prec */
+    int mrhs_kernel;        /* FP32 multi-RHS stencil (wilson_apply_n_arith, the FP32 batched paths):
+                               0 (default) chosen by the autotuner per lattice shape, 1 = right-hand
+                               sides in pairs looped inside each site's thread, 2 = blocks of 32 sites x
+                               one warp per right-hand side, 3 = each site's eight links staged in
+                               shared memory once, right-hand sides looped inside the thread */
 } ovl_params;
 
 /* Per-solve statistics (all fields written by ovl_solve when stats != NULL). */
@@ -230,6 +235,13 @@ ovl_status wilson_sap_apply(ovl_ctx *ctx, double *out, const double *in, double 
  * and the measured ms per full-lattice stencil application of each variant
  * (ms[0..3] = FP64 x1, FP64 x4, FP32 x1, FP32 x4; zeros when forced). Nullable outputs. */
 ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, float *ms);
+
+/* FP32 multi-RHS stencil kernel chosen for this lattice shape (params.mrhs_kernel numbering,
+ * 1..3) and the autotuner's measured ms per right-hand side of each candidate at 4 right-hand
+ * sides (ms[0..2] for kernels 1..3; zeros when params.mrhs_kernel forced the choice). The
+ * choice is an implementation detail of the multi-RHS stencil (the paper has no counterpart).
+ * Nullable outputs. */
+ovl_status ovl_tuning_mrhs(const ovl_ctx *ctx, int *kernel, float *ms);
 
 /* Deflation state (Sec. 5.2): k deflated pairs, their eigenvalues lambda[k] (signed, by
  * increasing modulus; nullable), |lambda_{k+1}| (the new lower end of the sign interval),

@@ -50,6 +50,7 @@ class ovl_params(ctypes.Structure):
         ("krylov_keep", ctypes.c_int), ("ff_outer", ctypes.c_int), ("max_seconds", ctypes.c_double),
         ("wilson_mg", ctypes.c_int), ("mg_nv", ctypes.c_int), ("mg_setup_iters", ctypes.c_int),
         ("mg_coarse_steps", ctypes.c_int), ("mg_coarse_tol", ctypes.c_double), ("m0_adapt", ctypes.c_int),
+        ("mrhs_kernel", ctypes.c_int),
     ]
 
 
@@ -111,7 +112,7 @@ class ovl_prof(ctypes.Structure):
 EXPORTS = ["ovl_params_default", "ovl_create", "wilson_apply", "sign_apply", "ovl_apply", "ovl_solve",
            "ovl_info", "ovl_zolotarev", "ovl_destroy", "ovl_last_error", "ovl_prof_enable", "ovl_prof_get",
            "wilson_solve", "ovl_tuning", "ovl_tuning_sap", "ovl_hermitian_eig", "ovl_deflation_info", "ovl_krylov_sign_info", "ovl_request_bytes", "wilson_sap_apply", "wilson_apply_noalloc", "ovl_dslash_time", "wilson_apply_n",
-           "ovl_apply_n", "ovl_dslash_time_n", "wilson_apply_arith", "wilson_apply_n_arith", "sign_apply_arith", "ovl_fma_peak", "ovl_mg_setup", "wilson_mg_apply", "ovl_mg_info", "ovl_m0_adapt_info", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
+           "ovl_apply_n", "ovl_dslash_time_n", "wilson_apply_arith", "wilson_apply_n_arith", "sign_apply_arith", "ovl_fma_peak", "ovl_mg_setup", "wilson_mg_apply", "ovl_mg_info", "ovl_m0_adapt_info", "ovl_tuning_mrhs", "ovl_server_create", "ovl_server_submit", "ovl_server_query",
            "ovl_server_wait", "ovl_server_report", "ovl_server_destroy"]
 
 _lib = None
@@ -142,6 +143,7 @@ def lib():
         L.wilson_sap_apply.argtypes = [P, P, P, D]
         L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
         L.ovl_tuning_sap.argtypes = [P, ctypes.POINTER(I_), P]
+        L.ovl_tuning_mrhs.argtypes = [P, ctypes.POINTER(I_), P]
         L.ovl_hermitian_eig.argtypes = [I_, P, P, P]
         L.ovl_deflation_info.argtypes = [P, ctypes.POINTER(I_), P, ctypes.POINTER(D), ctypes.POINTER(D),
                                          ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
@@ -405,6 +407,16 @@ def ovl_krylov_sign_info(ctx):
     return {"cycles": cyc.value, "matvecs": mv.value}
 
 
+def ovl_tuning_mrhs(ctx):
+    """FP32 multi-RHS stencil kernel chosen for this lattice shape (1 RHS pairs, 2 tiles of 32
+    sites, 3 staged links) and the timed ms per right-hand side of each candidate."""
+    import numpy as np
+    k = ctypes.c_int()
+    ms = np.zeros(3, dtype=np.float32)
+    _check(lib().ovl_tuning_mrhs(ctx, ctypes.byref(k), _ptr(ms)), ctx)
+    return {"kernel": k.value, "ms": ms.tolist()}
+
+
 def ovl_tuning_sap(ctx):
     """Threads per block site of the FP32 Schwarz block solves and the timed variants (ms)."""
     import numpy as np
@@ -534,6 +546,9 @@ class Overlap:
 
     def tuning_sap(self):
         return ovl_tuning_sap(self.ctx)
+
+    def tuning_mrhs(self):
+        return ovl_tuning_mrhs(self.ctx)
 
     def deflation_info(self):
         return ovl_deflation_info(self.ctx)

@@ -80,6 +80,7 @@ extern "C" ovl_status ovl_params_default(ovl_params *p) {
     p->mg_coarse_steps = 16;
     p->mg_coarse_tol = 0.1;
     p->m0_adapt = 0;
+    p->mrhs_kernel = 0;
     return OVL_OK;
 }
 
@@ -118,6 +119,7 @@ static ovl_status validate_params(const ovl_params &p, const int L[4], std::stri
     if (p.mg_coarse_steps < 1 || p.mg_coarse_steps > kMgMaxSteps) { err = "mg_coarse_steps must be in [1, 64]"; return OVL_EINVAL; }
     if (!(p.mg_coarse_tol >= 0 && p.mg_coarse_tol < 1)) { err = "mg_coarse_tol must be in [0, 1)"; return OVL_EINVAL; }
     if (p.m0_adapt != 0 && p.m0_adapt != 1) { err = "m0_adapt must be 0 or 1"; return OVL_EINVAL; }
+    if (p.mrhs_kernel < 0 || p.mrhs_kernel > 3) { err = "mrhs_kernel must be in [0, 3]"; return OVL_EINVAL; }
     if (p.wilson_mg) {
         for (int m = 0; m < 4; m++)
             if (p.sap_block[m] < 2 || (p.sap_block[m] & 1) || L[m] % p.sap_block[m] || L[m] / p.sap_block[m] < 2) {
@@ -976,6 +978,68 @@ ovl_status Ctx::autotune() {
     return OVL_OK;
 }
 
+// FP32 multi-RHS stencil kernel (Geom::mrhs32): each of the three kernels is timed on four
+// right-hand sides of seeded pseudo-random fields and the fastest per right-hand side kept.
+// Cached per process and lattice shape; the first context of a shape to finish fixes the choice
+// (as for the threads per site), so every context of that shape runs the same kernel.
+static std::map<std::tuple<int, int, int, int>, std::pair<int, std::array<float, 3>>> g_mrhs_cache;
+ovl_status Ctx::autotune_mrhs() {
+    Ctx *c = this;
+    const auto key = std::make_tuple(g.L[0], g.L[1], g.L[2], g.L[3]);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_mrhs_cache.find(key);
+        if (it != g_mrhs_cache.end()) {
+            g.mrhs32 = it->second.first;
+            for (int k = 0; k < 3; k++) tune_mrhs_ms[k] = it->second.second[k];
+            return OVL_OK;
+        }
+    }
+    constexpr int nr = 4;
+    const long w = (long)g.V * 6;   // float4 words per FP32 vector
+    void *buf;
+    ST(alloc(&buf, (size_t)w * 2 * nr * sizeof(float4)));
+    float4 *fin = (float4 *)buf, *fout = fin + w * nr;
+    CK(fill_random_f32((float *)fin, 4 * w * nr, 7301, stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int reps = g.V >= (1 << 20) ? 3 : 10;
+    float ms[3] = {0, 0, 0};
+    for (int v = 0; v < 3; v++) {
+        Geom gg = g;
+        gg.mrhs32 = v + 1;
+        for (int k = 0; k < 2 + reps; k++) {
+            if (k == 2) CK(cudaEventRecord(e0, stream));
+            CK(wilson_batch_f32(gg, U32, fin, fout, w, nr, (float)m0_ker, 0, 1.f, nullptr, 0.f, stream));
+        }
+        CK(cudaEventRecord(e1, stream));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms[v], e0, e1));
+        ms[v] /= (float)(reps * nr);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int best = 0;
+    for (int v = 1; v < 3; v++)
+        if (ms[v] < ms[best]) best = v;
+    g.mrhs32 = best + 1;
+    for (int k = 0; k < 3; k++) tune_mrhs_ms[k] = ms[k];
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_mrhs_cache.find(key);
+        if (it != g_mrhs_cache.end()) {
+            g.mrhs32 = it->second.first;
+            for (int k = 0; k < 3; k++) tune_mrhs_ms[k] = it->second.second[k];
+        } else {
+            g_mrhs_cache[key] = {g.mrhs32, {ms[0], ms[1], ms[2]}};
+        }
+    }
+    cudaFree(buf);
+    allocs.erase(std::find(allocs.begin(), allocs.end(), buf));
+    return OVL_OK;
+}
+
 // Threads per site of the FP32 Schwarz block kernel (1, 2 or 4): one Schwarz cycle of
 // each variant is timed on a constant non-zero input and the fastest kept. Cached per
 // process, lattice shape and block shape.
@@ -1174,6 +1238,8 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
     c->g.tps64 = c->g.tps32 = 1;
     if (c->p.stencil_tps) c->g.tps64 = c->g.tps32 = c->p.stencil_tps;
     else ST(c->autotune());
+    if (c->p.mrhs_kernel) c->g.mrhs32 = c->p.mrhs_kernel;
+    else ST(c->autotune_mrhs());
     if (c->p.sap_tps) {
         c->sap_tps = c->p.sap_tps;
         c->sap_tuned = true;
@@ -1363,6 +1429,15 @@ extern "C" ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, flo
     if (tps32) *tps32 = c->g.tps32;
     if (ms)
         for (int k = 0; k < 4; k++) ms[k] = c->tune_ms[k];
+    return OVL_OK;
+}
+
+extern "C" ovl_status ovl_tuning_mrhs(const ovl_ctx *ctx, int *kernel, float *ms) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c) return OVL_EINVAL;
+    if (kernel) *kernel = c->g.mrhs32;
+    if (ms)
+        for (int k = 0; k < 3; k++) ms[k] = c->tune_mrhs_ms[k];
     return OVL_OK;
 }
 

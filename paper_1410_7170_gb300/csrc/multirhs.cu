@@ -2,9 +2,12 @@
 // multishift CG that runs one independent Zolotarev sign evaluation per right-hand side
 // in lock-step.
 //
-// The FP32 multi-RHS stencil loops over the right-hand sides inside each thread (see
-// k_wilson_mrhs_pairs). The FP64 stencil and the batched multishift kernels use thread blocks
-// of 32 sites x nr right-hand sides (threadIdx.x = site, threadIdx.y = right-hand side). The nr threads of one site need the same eight links; running them
+// The FP32 multi-RHS stencil has three kernels, chosen per lattice shape by the autotuner
+// (Geom::mrhs32): the right-hand sides in pairs looped inside each site's thread
+// (k_wilson_mrhs_pairs), blocks of 32 sites x one warp per right-hand side (k_wilson_mrhs), or
+// the links staged in shared memory with the right-hand sides looped (k_wilson_mrhs_links).
+// The FP64 stencil and the batched multishift kernels use thread blocks of 32 sites x nr
+// right-hand sides (threadIdx.x = site, threadIdx.y = right-hand side). The nr threads of one site need the same eight links; running them
 // in one block makes the repeats hit L1, so DRAM sees each link once per block of
 // right-hand sides: per site and right-hand side the stencil moves 48 / nr link reals
 // plus 48 spinor reals instead of 96. Each warp holds one right-hand side, so warp sums
@@ -89,6 +92,109 @@ __global__ void __launch_bounds__(kBlock, 2) k_wilson_mrhs_pairs(Geom g, const f
             }
             store_spinor<float>(out + rhs * stride, g.Vh, p, i, res);
         }
+    }
+}
+
+// FP32 multi-RHS stencil with the links staged per thread: each thread owns one site in the
+// single-RHS order, copies its eight links (4 forward at the site, 4 backward at the neighbours,
+// rows 0-1: 24 words) and its eight neighbour indices into its own column of shared memory once,
+// and applies them to every right-hand side in turn, so the links leave L2 once per launch
+// instead of once per right-hand side. The shared memory (about 100 KB per 256-thread block)
+// comes out of L1, which the neighbour spinors would otherwise hit in: measured at 12
+// right-hand sides it is the best of the three kernels at 16^4 and the worst at 32^4 and above,
+// which is why the autotuner chooses per lattice shape.
+constexpr int kLinkSlotWords = 24;
+
+template <int MU>
+__device__ __forceinline__ void hop_dir_slot(const Geom &g, const float4 *__restrict__ in, int q, const int *nb,
+                                             int x0, const float4 *sl, int S, cpx<float> acc[12]) {
+    const int jf = nb[MU * S], jb = nb[(4 + MU) * S];
+    {   // forward: link words MU*3 .. MU*3+2
+        cpx<float> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
+        load_spinor<float>(in, g.Vh, q, jf, s);
+        proj_fwd(MU, s, h0, h1);
+        if (MU == 0) flip_half(h0, h1, g.antiperiodic && x0 == g.L[0] - 1);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float4 v = sl[(MU * 3 + c) * S];
+            u[(2 * c) / 3][(2 * c) % 3] = cpx<float>{v.x, v.y};
+            u[(2 * c + 1) / 3][(2 * c + 1) % 3] = cpx<float>{v.z, v.w};
+        }
+        reconstruct_row2(u);
+        su3_mul(u, h0, a0);
+        su3_mul(u, h1, a1);
+        acc_fwd<MU == 0>(MU, acc, a0, a1);
+    }
+    {   // backward: link words 12 + MU*3 ..
+        cpx<float> s[12], h0[3], h1[3], a0[3], a1[3], u[3][3];
+        load_spinor<float>(in, g.Vh, q, jb, s);
+        proj_bwd(MU, s, h0, h1);
+        if (MU == 0) flip_half(h0, h1, g.antiperiodic && x0 == 0);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float4 v = sl[(12 + MU * 3 + c) * S];
+            u[(2 * c) / 3][(2 * c) % 3] = cpx<float>{v.x, v.y};
+            u[(2 * c + 1) / 3][(2 * c + 1) % 3] = cpx<float>{v.z, v.w};
+        }
+        reconstruct_row2(u);
+        su3_dag_mul(u, h0, a0);
+        su3_dag_mul(u, h1, a1);
+        acc_bwd(MU, acc, a0, a1);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock, 2) k_wilson_mrhs_links(Geom g, const float4 *__restrict__ U,
+                                                               const float4 *__restrict__ in, float4 *__restrict__ out,
+                                                               long stride, int nrhs, float m4, int g5, float a,
+                                                               const float4 *z, float b, int spb) {
+    // [kLinkSlotWords][blockDim.x] links, then [8][blockDim.x] neighbour indices (forward, backward)
+    extern __shared__ float4 link_slots[];
+    const int t = blockIdx.x * spb + threadIdx.x;
+    if (threadIdx.x >= spb || t >= g.V) return;
+    int p, i;
+    site_of_thread(t, p, i);
+    int x[4];
+    eo_coords(g, p, i, x);
+    const int q = 1 - p, S = blockDim.x;
+    float4 *sl = link_slots + threadIdx.x;
+    int *nb = reinterpret_cast<int *>(link_slots + kLinkSlotWords * S) + threadIdx.x;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        int y[4] = {x[0], x[1], x[2], x[3]};
+        y[mu] = x[mu] + 1 == g.L[mu] ? 0 : x[mu] + 1;
+        nb[mu * S] = eo_index(g, y);
+        y[mu] = x[mu] == 0 ? g.L[mu] - 1 : x[mu] - 1;
+        const int jb = eo_index(g, y);
+        nb[(4 + mu) * S] = jb;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            sl[(mu * 3 + c) * S] = __ldg(U + ((size_t)(p * 4 + mu) * 3 + c) * g.Vh + i);
+            sl[(12 + mu * 3 + c) * S] = __ldg(U + ((size_t)(q * 4 + mu) * 3 + c) * g.Vh + jb);
+        }
+    }
+    const int x0 = x[0];
+    // each thread reads back only its own column: no barrier needed
+#pragma unroll 1
+    for (int r = 0; r < nrhs; r++) {
+        const float4 *xin = in + r * stride;
+        cpx<float> acc[12], own[12], res[12];
+        hop_dir_slot<0>(g, xin, q, nb, x0, sl, S, acc);
+        hop_dir_slot<1>(g, xin, q, nb, x0, sl, S, acc);
+        hop_dir_slot<2>(g, xin, q, nb, x0, sl, S, acc);
+        hop_dir_slot<3>(g, xin, q, nb, x0, sl, S, acc);
+        load_spinor<float>(xin, g.Vh, p, i, own);
+        wilson_combine<float>(m4, own, acc, res);
+        if (g5) apply_g5(res);
+        if (z) {
+            cpx<float> zz[12];
+            load_spinor<float>(z + r * stride, g.Vh, p, i, zz);
+#pragma unroll
+            for (int c = 0; c < 12; c++) res[c] = a * res[c] + b * zz[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 12; c++) res[c] = a * res[c];
+        }
+        store_spinor<float>(out + r * stride, g.Vh, p, i, res);
     }
 }
 
@@ -418,7 +524,21 @@ cudaError_t wilson_batch_f64(const Geom &g, const double2 *U, const double2 *in,
 }
 cudaError_t wilson_batch_f32(const Geom &g, const float4 *U, const float4 *in, float4 *out, long stride, int nrhs,
                              float m0, int g5, float a, const float4 *z, float b, cudaStream_t st) {
-    if (nrhs > 1) {
+    if (nrhs > 1 && g.mrhs32 == 3) {
+        static unsigned attr_set = 0;   // devices whose dynamic shared memory limit is raised
+        int dev = 0;
+        const int most = kBlock * (kLinkSlotWords * (int)sizeof(float4) + 8 * (int)sizeof(int));
+        if (cudaGetDevice(&dev) == cudaSuccess && dev < 32 && !(attr_set & (1u << dev))) {
+            const cudaError_t e = cudaFuncSetAttribute(k_wilson_mrhs_links, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       most);
+            if (e != cudaSuccess) return e;
+            attr_set |= 1u << dev;
+        }
+        const LaunchShape ls = balanced_shape(g.V, g.nsm, 2, 1 << 30);
+        const size_t smem = (size_t)ls.block * (kLinkSlotWords * sizeof(float4) + 8 * sizeof(int));
+        k_wilson_mrhs_links<<<ls.grid, ls.block, smem, st>>>(g, U, in, out, stride, nrhs, m0 + 4.f, g5, a, z, b,
+                                                             ls.spb);
+    } else if (nrhs > 1 && g.mrhs32 != 2) {
         const LaunchShape ls = balanced_shape(g.V, g.nsm, 2, 1 << 30);
         k_wilson_mrhs_pairs<<<ls.grid, ls.block, 0, st>>>(g, U, in, out, stride, nrhs, m0 + 4.f, g5, a, z, b,
                                                           ls.spb);

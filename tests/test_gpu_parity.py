@@ -438,7 +438,13 @@ def test_autotuner_reports_a_choice():
     t = op.tuning()
     assert t["tps64"] in (1, 4) and t["tps32"] in (1, 4)
     assert all(m > 0 for m in t["ms"])
+    t = op.tuning_mrhs()   # multi-RHS kernel: the fastest of the three timed per right-hand side
+    assert t["kernel"] in (1, 2, 3) and all(m > 0 for m in t["ms"])
+    assert t["ms"][t["kernel"] - 1] == min(t["ms"])
     op.close()
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.Overlap(U, dims, 1.0, 0.01, params(mrhs_kernel=4))
+    assert e.value.status == ovl.OVL_EINVAL
     op = ovl.Overlap(U, dims, 1.0, 0.01, params(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32))
     t = op.tuning_sap()
     assert t["sap_tps"] in (1, 2, 4) and all(m > 0 for m in t["ms"])

@@ -82,16 +82,19 @@ def test_wilson_arith_matches_oracle(dims, ap, m0, arith, tps, bar):
     op.close()
 
 
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 @pytest.mark.parametrize("nrhs", [1, 2, 3, 4, 7, 12, 13])
-def test_wilson_multi_rhs_fp32_matches_oracle(nrhs):
-    """The FP32 multi-RHS stencil (two right-hand sides per thread share each link load),
-    blocks of up to 12 per launch (13 = a full block and a ragged one), every right-hand
-    side against the oracle."""
+def test_wilson_multi_rhs_fp32_matches_oracle(nrhs, kernel):
+    """The three FP32 multi-RHS stencil kernels (right-hand-side pairs sharing each link load;
+    32-site tiles with a warp per right-hand side; links staged in shared memory), blocks of up
+    to 12 per launch (13 = a full block and a ragged one), every right-hand side against the
+    oracle."""
     dims = (8, 8, 8, 8)
     U = synth.gauge_field(dims, 0.5, 1300, stout_steps=1)
     psi = np.stack([synth.rhs_gaussian(dims, 1400 + k) for k in range(nrhs)])
-    p = ovl.params_default(lambda_min=0.05, lambda_max=8.0)
+    p = ovl.params_default(lambda_min=0.05, lambda_max=8.0, mrhs_kernel=kernel)
     op = ovl.Overlap(U, dims, 1.0, 0.05, p)
+    assert op.tuning_mrhs()["kernel"] == kernel
     out = torch.empty_like(dev(psi))
     op.wilson_apply_n_arith(out, dev(psi), nrhs, -0.7, ovl.OVL_ARITH_FP32)
     o = host(out)
@@ -103,8 +106,8 @@ def test_wilson_multi_rhs_fp32_matches_oracle(nrhs):
 
 def test_wilson_multi_rhs_fp32_at_32x32x32x32():
     """Full 32^4 size with 12 right-hand sides in one launch (the 12-point-source workload's
-    stencil): three of the outputs compared element by element with the oracle's
-    definitional stencil on the whole lattice."""
+    stencil, with the kernel the autotuner picks): three of the outputs compared element by
+    element with the oracle's definitional stencil on the whole lattice."""
     dims = (32, 32, 32, 32)
     U = synth.gauge_field(dims, 0.5, 1003, stout_steps=3, device="cuda")
     nrhs = 12
