@@ -238,7 +238,7 @@ def run_ours(args, rank, world, dist):
     op = ovl.Overlap(torch.from_numpy(U).to(dev), DIMS, 1.0, 0.01, solver_params(ovl, True),
                      stream=stream.cuda_stream)
     info = op.info()
-    tuning, tuning_sap = op.tuning(), op.tuning_sap()
+    tuning, tuning_sap, tuning_mrhs = op.tuning(), op.tuning_sap(), op.tuning_mrhs()
     with Clocks(dev_idx) as clk:
         ms_mixed, st_mixed, prof = timed_solves(op, args.steps, args.warmup, prof=True)
     clocks = clk.summary()
@@ -347,7 +347,7 @@ def run_ours(args, rank, world, dist):
                            "hbm_gbs": pk["hbm_gbs"]},
         "mixed_stats": {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in st_mixed[-1].items()},
         "tuning": {"stencil_tps_fp64": tuning["tps64"], "stencil_tps_fp32": tuning["tps32"],
-                   "sap_tps": tuning_sap["sap_tps"]},
+                   "sap_tps": tuning_sap["sap_tps"], "fp32_multi_rhs_kernel": tuning_mrhs},
     }
     out["dslash"] = dslash(ovl, torch, dev, pk["hbm_gbs"])
     out["sign_methods"] = sign_methods(ovl, torch, U, b, dev, stream, info)
@@ -513,6 +513,8 @@ def dslash(ovl, torch, dev, hbm_gbs, dims=(64, 32, 32, 32)):
         ms = op.dslash_time_n(1, nr, 10)
         gbs = (48.0 / nr + 48.0) * nr * V * 4 / (ms * 1e-3) / 1e9
         out["fp32_rhs%d" % nr] = {"ms": ms, "ms_per_rhs": ms / nr, "GB/s": gbs, "frac_hbm": gbs / hbm_gbs}
+    # the autotuner's multi-RHS kernel per block size (1 RHS pairs, 2 32-site tiles, 3 staged links)
+    out["fp32_multi_rhs_kernels"] = op.tuning_mrhs()
     op.close()
     return out
 
@@ -567,7 +569,7 @@ def serving(ovl, torch, dev, n_req=24, slots=3, seed=5000):
             "completed": st["completed"], "failed": st["failed"], "hbm_high_water_bytes": st["hbm_high_water"]}
 
 
-def serving_full(seed=5000, n_req=200, slots=3, n_cap=40, n_alone=8):
+def serving_full(seed=5000, n_req=200, slots=3, n_cap=20, n_alone=8):
     """The full serving workload: Poisson arrivals of n_req overlap solves, lattice V uniform in
     {8^4, 16^4, 24^4, 32^4}, mu in {0.01, 0.05, 0.1}, 1-12 Gaussian right-hand sides, each
     request with its own gauge field (generator seeded by the request id, 3 stout steps), tol
@@ -583,6 +585,12 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=40, n_alone=8):
     import synth
 
     build.build()
+    t_start = time.perf_counter()
+
+    def stage(msg, **kw):   # progress on stderr, so a cut-short run still tells how far it got
+        print(json.dumps({"stage": msg, "t_s": round(time.perf_counter() - t_start, 1), **kw}), file=sys.stderr,
+              flush=True)
+
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(seed)
     sizes = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 32)]
@@ -616,10 +624,14 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=40, n_alone=8):
         srv.close()
         return rep, res, xs
 
+    stage("inputs resident")
     run(reqs[:6], 0.0)                                   # warm-up: tuning of every lattice shape
+    stage("warm-up done")
     cap, _, _ = run(reqs[:n_cap], 0.0)
     rate = 0.7 * cap["solves_per_s"]
+    stage("capacity measured", solves_per_s=cap["solves_per_s"])
     rep, res, xs = run(reqs, rate)
+    stage("stream done", p50_s=rep["p50_s"], p99_s=rep["p99_s"], solves_per_s=rep["solves_per_s"])
     worst_res = max(x["stats"]["true_rel_resid"] for x in res)
     # a sample of requests re-run alone: the served result must be the same, bit for bit
     diffs = []
