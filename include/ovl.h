@@ -165,7 +165,8 @@ typedef struct {
                                estimate per second of the iteration it served; the scores persist in
                                the context across solves. 0 (default): always m0_prec */
     int mrhs_kernel;        /* FP32 multi-RHS stencil (wilson_apply_n_arith, the FP32 batched paths):
-                               0 (default) chosen by the autotuner per lattice shape, 1 = right-hand
+                               0 (default) chosen by the autotuner per lattice shape and block size
+                               (up to 6 right-hand sides, 7..12; see ovl_tuning_mrhs), 1 = right-hand
                                sides in pairs looped inside each site's thread, 2 = blocks of 32 sites x
                                one warp per right-hand side, 3 = each site's eight links staged in
                                shared memory once, right-hand sides looped inside the thread */
@@ -236,11 +237,12 @@ ovl_status wilson_sap_apply(ovl_ctx *ctx, double *out, const double *in, double 
  * (ms[0..3] = FP64 x1, FP64 x4, FP32 x1, FP32 x4; zeros when forced). Nullable outputs. */
 ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, float *ms);
 
-/* FP32 multi-RHS stencil kernel chosen for this lattice shape (params.mrhs_kernel numbering,
- * 1..3) and the autotuner's measured ms per right-hand side of each candidate at 4 right-hand
- * sides (ms[0..2] for kernels 1..3; zeros when params.mrhs_kernel forced the choice). The
+/* FP32 multi-RHS stencil kernels chosen for this lattice shape (params.mrhs_kernel numbering,
+ * 1..3): kernel[0] for blocks of up to 6 right-hand sides, kernel[1] for 7..12; and the
+ * autotuner's measured ms per right-hand side of each candidate, ms[0..2] at 4 right-hand sides
+ * and ms[3..5] at 12 (kernels 1..3; zeros when params.mrhs_kernel forced the choice). The
  * choice is an implementation detail of the multi-RHS stencil (the paper has no counterpart).
- * Nullable outputs. */
+ * Nullable outputs (kernel: 2 ints, ms: 6 floats). */
 ovl_status ovl_tuning_mrhs(const ovl_ctx *ctx, int *kernel, float *ms);
 
 /* Deflation state (Sec. 5.2): k deflated pairs, their eigenvalues lambda[k] (signed, by

@@ -143,7 +143,7 @@ def lib():
         L.wilson_sap_apply.argtypes = [P, P, P, D]
         L.ovl_tuning.argtypes = [P, ctypes.POINTER(I_), ctypes.POINTER(I_), P]
         L.ovl_tuning_sap.argtypes = [P, ctypes.POINTER(I_), P]
-        L.ovl_tuning_mrhs.argtypes = [P, ctypes.POINTER(I_), P]
+        L.ovl_tuning_mrhs.argtypes = [P, P, P]
         L.ovl_hermitian_eig.argtypes = [I_, P, P, P]
         L.ovl_deflation_info.argtypes = [P, ctypes.POINTER(I_), P, ctypes.POINTER(D), ctypes.POINTER(D),
                                          ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
@@ -408,13 +408,14 @@ def ovl_krylov_sign_info(ctx):
 
 
 def ovl_tuning_mrhs(ctx):
-    """FP32 multi-RHS stencil kernel chosen for this lattice shape (1 RHS pairs, 2 tiles of 32
-    sites, 3 staged links) and the timed ms per right-hand side of each candidate."""
+    """FP32 multi-RHS stencil kernels chosen for this lattice shape (1 RHS pairs, 2 tiles of 32
+    sites, 3 staged links) for blocks of up to 6 and of 7..12 right-hand sides, and the timed ms
+    per right-hand side of each candidate at 4 and at 12."""
     import numpy as np
-    k = ctypes.c_int()
-    ms = np.zeros(3, dtype=np.float32)
-    _check(lib().ovl_tuning_mrhs(ctx, ctypes.byref(k), _ptr(ms)), ctx)
-    return {"kernel": k.value, "ms": ms.tolist()}
+    k = np.zeros(2, dtype=np.int32)
+    ms = np.zeros(6, dtype=np.float32)
+    _check(lib().ovl_tuning_mrhs(ctx, _ptr(k), _ptr(ms)), ctx)
+    return {"kernel": int(k[0]), "kernel_large": int(k[1]), "ms4": ms[:3].tolist(), "ms12": ms[3:].tolist()}
 
 
 def ovl_tuning_sap(ctx):

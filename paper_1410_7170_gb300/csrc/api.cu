@@ -978,11 +978,14 @@ ovl_status Ctx::autotune() {
     return OVL_OK;
 }
 
-// FP32 multi-RHS stencil kernel (Geom::mrhs32): each of the three kernels is timed on four
-// right-hand sides of seeded pseudo-random fields and the fastest per right-hand side kept.
-// Cached per process and lattice shape; the first context of a shape to finish fixes the choice
-// (as for the threads per site), so every context of that shape runs the same kernel.
-static std::map<std::tuple<int, int, int, int>, std::pair<int, std::array<float, 3>>> g_mrhs_cache;
+// FP32 multi-RHS stencil kernels (Geom::mrhs32 for blocks of up to 6 right-hand sides,
+// mrhs32l for 7..12): each of the three kernels is timed on 4 and on 12 right-hand sides of
+// seeded pseudo-random fields and the fastest per right-hand side kept for each block size
+// (their order changes with the block: at 64x32^3 the 32-site tiles are the fastest at 4 and
+// the slowest at 12). Cached per process and lattice shape; the first context of a shape to
+// finish fixes the choice (as for the threads per site), so every context of that shape runs
+// the same kernels.
+static std::map<std::tuple<int, int, int, int>, std::pair<std::array<int, 2>, std::array<float, 6>>> g_mrhs_cache;
 ovl_status Ctx::autotune_mrhs() {
     Ctx *c = this;
     const auto key = std::make_tuple(g.L[0], g.L[1], g.L[2], g.L[3]);
@@ -990,49 +993,55 @@ ovl_status Ctx::autotune_mrhs() {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_mrhs_cache.find(key);
         if (it != g_mrhs_cache.end()) {
-            g.mrhs32 = it->second.first;
-            for (int k = 0; k < 3; k++) tune_mrhs_ms[k] = it->second.second[k];
+            g.mrhs32 = it->second.first[0];
+            g.mrhs32l = it->second.first[1];
+            for (int k = 0; k < 6; k++) tune_mrhs_ms[k] = it->second.second[k];
             return OVL_OK;
         }
     }
-    constexpr int nr = 4;
+    constexpr int nmax = 12;
     const long w = (long)g.V * 6;   // float4 words per FP32 vector
     void *buf;
-    ST(alloc(&buf, (size_t)w * 2 * nr * sizeof(float4)));
-    float4 *fin = (float4 *)buf, *fout = fin + w * nr;
-    CK(fill_random_f32((float *)fin, 4 * w * nr, 7301, stream));
+    ST(alloc(&buf, (size_t)w * 2 * nmax * sizeof(float4)));
+    float4 *fin = (float4 *)buf, *fout = fin + w * nmax;
+    CK(fill_random_f32((float *)fin, 4 * w * nmax, 7301, stream));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int reps = g.V >= (1 << 20) ? 3 : 10;
-    float ms[3] = {0, 0, 0};
-    for (int v = 0; v < 3; v++) {
-        Geom gg = g;
-        gg.mrhs32 = v + 1;
-        for (int k = 0; k < 2 + reps; k++) {
-            if (k == 2) CK(cudaEventRecord(e0, stream));
-            CK(wilson_batch_f32(gg, U32, fin, fout, w, nr, (float)m0_ker, 0, 1.f, nullptr, 0.f, stream));
+    float ms[6] = {0, 0, 0, 0, 0, 0};
+    int best[2] = {0, 0};
+    for (int sz = 0; sz < 2; sz++) {
+        const int nr = sz ? nmax : 4;
+        for (int v = 0; v < 3; v++) {
+            Geom gg = g;
+            gg.mrhs32 = gg.mrhs32l = v + 1;
+            for (int k = 0; k < 2 + reps; k++) {
+                if (k == 2) CK(cudaEventRecord(e0, stream));
+                CK(wilson_batch_f32(gg, U32, fin, fout, w, nr, (float)m0_ker, 0, 1.f, nullptr, 0.f, stream));
+            }
+            CK(cudaEventRecord(e1, stream));
+            CK(cudaEventSynchronize(e1));
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            ms[3 * sz + v] = t / (float)(reps * nr);
+            if (ms[3 * sz + v] < ms[3 * sz + best[sz]]) best[sz] = v;
         }
-        CK(cudaEventRecord(e1, stream));
-        CK(cudaEventSynchronize(e1));
-        CK(cudaEventElapsedTime(&ms[v], e0, e1));
-        ms[v] /= (float)(reps * nr);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int best = 0;
-    for (int v = 1; v < 3; v++)
-        if (ms[v] < ms[best]) best = v;
-    g.mrhs32 = best + 1;
-    for (int k = 0; k < 3; k++) tune_mrhs_ms[k] = ms[k];
+    g.mrhs32 = best[0] + 1;
+    g.mrhs32l = best[1] + 1;
+    for (int k = 0; k < 6; k++) tune_mrhs_ms[k] = ms[k];
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_mrhs_cache.find(key);
         if (it != g_mrhs_cache.end()) {
-            g.mrhs32 = it->second.first;
-            for (int k = 0; k < 3; k++) tune_mrhs_ms[k] = it->second.second[k];
+            g.mrhs32 = it->second.first[0];
+            g.mrhs32l = it->second.first[1];
+            for (int k = 0; k < 6; k++) tune_mrhs_ms[k] = it->second.second[k];
         } else {
-            g_mrhs_cache[key] = {g.mrhs32, {ms[0], ms[1], ms[2]}};
+            g_mrhs_cache[key] = {{g.mrhs32, g.mrhs32l}, {ms[0], ms[1], ms[2], ms[3], ms[4], ms[5]}};
         }
     }
     cudaFree(buf);
@@ -1238,7 +1247,7 @@ static ovl_status create_impl(Ctx *c, const double *gauge, const int dims[4], do
     c->g.tps64 = c->g.tps32 = 1;
     if (c->p.stencil_tps) c->g.tps64 = c->g.tps32 = c->p.stencil_tps;
     else ST(c->autotune());
-    if (c->p.mrhs_kernel) c->g.mrhs32 = c->p.mrhs_kernel;
+    if (c->p.mrhs_kernel) c->g.mrhs32 = c->g.mrhs32l = c->p.mrhs_kernel;
     else ST(c->autotune_mrhs());
     if (c->p.sap_tps) {
         c->sap_tps = c->p.sap_tps;
@@ -1435,9 +1444,12 @@ extern "C" ovl_status ovl_tuning(const ovl_ctx *ctx, int *tps64, int *tps32, flo
 extern "C" ovl_status ovl_tuning_mrhs(const ovl_ctx *ctx, int *kernel, float *ms) {
     const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
     if (!c) return OVL_EINVAL;
-    if (kernel) *kernel = c->g.mrhs32;
+    if (kernel) {
+        kernel[0] = c->g.mrhs32;
+        kernel[1] = c->g.mrhs32l;
+    }
     if (ms)
-        for (int k = 0; k < 3; k++) ms[k] = c->tune_mrhs_ms[k];
+        for (int k = 0; k < 6; k++) ms[k] = c->tune_mrhs_ms[k];
     return OVL_OK;
 }
 

@@ -64,7 +64,9 @@ struct Geom {
     int V;
     int antiperiodic;
     int tps64, tps32;   // threads per site of the FP64 / FP32 stencils (1 or 4), chosen by the autotuner
-    int mrhs32;         // FP32 multi-RHS stencil kernel (1 RHS pairs, 2 tiles of 32 sites, 3 staged links)
+    int mrhs32;         // FP32 multi-RHS stencil kernel for <= 6 right-hand sides (1 RHS pairs, 2 tiles of 32
+                        // sites, 3 staged links); mrhs32l for 7..12
+    int mrhs32l;
     int nsm;            // streaming multiprocessors of the device (grid sizing)
 };
 

@@ -524,7 +524,8 @@ cudaError_t wilson_batch_f64(const Geom &g, const double2 *U, const double2 *in,
 }
 cudaError_t wilson_batch_f32(const Geom &g, const float4 *U, const float4 *in, float4 *out, long stride, int nrhs,
                              float m0, int g5, float a, const float4 *z, float b, cudaStream_t st) {
-    if (nrhs > 1 && g.mrhs32 == 3) {
+    const int kern = nrhs > 6 ? g.mrhs32l : g.mrhs32;
+    if (nrhs > 1 && kern == 3) {
         static unsigned attr_set = 0;   // devices whose dynamic shared memory limit is raised
         int dev = 0;
         const int most = kBlock * (kLinkSlotWords * (int)sizeof(float4) + 8 * (int)sizeof(int));
@@ -538,7 +539,7 @@ cudaError_t wilson_batch_f32(const Geom &g, const float4 *U, const float4 *in, f
         const size_t smem = (size_t)ls.block * (kLinkSlotWords * sizeof(float4) + 8 * sizeof(int));
         k_wilson_mrhs_links<<<ls.grid, ls.block, smem, st>>>(g, U, in, out, stride, nrhs, m0 + 4.f, g5, a, z, b,
                                                              ls.spb);
-    } else if (nrhs > 1 && g.mrhs32 != 2) {
+    } else if (nrhs > 1 && kern != 2) {
         const LaunchShape ls = balanced_shape(g.V, g.nsm, 2, 1 << 30);
         k_wilson_mrhs_pairs<<<ls.grid, ls.block, 0, st>>>(g, U, in, out, stride, nrhs, m0 + 4.f, g5, a, z, b,
                                                           ls.spb);

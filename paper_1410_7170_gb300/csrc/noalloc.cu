@@ -125,7 +125,7 @@ extern "C" ovl_status wilson_apply_noalloc(double *out, const double *in, const 
     g.Lh3 = dims[3] / 2;
     g.antiperiodic = antiperiodic ? 1 : 0;
     g.tps64 = g.tps32 = 1;
-    g.mrhs32 = 1;
+    g.mrhs32 = g.mrhs32l = 1;
     if (cudaDeviceGetAttribute(&g.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return fail(OVL_ECUDA, "wilson_apply_noalloc: cannot query the device");

@@ -95,7 +95,7 @@ size_t estimate_bytes(const ovl_request &r, const ovl_params &p) {
     const double v64 = 24.0 * V * 8.0, v32 = 24.0 * V * 4.0;
     double b = V * 4 * (9 * 16 + 3 * 16);                 // links: FP64 18 reals + FP32 12 reals
     b += 3 * v64 + 6 * v32;                               // staging, Lanczos / tuning vectors
-    b += 8 * v32;                                         // multi-RHS stencil tuning (4 RHS in and out)
+    b += 24 * v32;                                        // multi-RHS stencil tuning (12 RHS in and out)
     b += (p.n_poles + 3) * v64;                           // FP64 (or float-float) multishift
     const bool mixed = p.precision != OVL_FP64 || p.precond == OVL_PREC_RECURSIVE;
     if (mixed) b += (p.n_poles + 4) * v32;                 // FP32 multishift

@@ -143,7 +143,8 @@ struct Ctx {
     long stat_ms64 = 0, stat_ms32 = 0, stat_msff = 0, stat_prec = 0;
     int stat_inner = 0;
     float tune_ms[4] = {0, 0, 0, 0};   // stencil ms: fp64 1/4 tps, fp32 1/4 tps
-    float tune_mrhs_ms[3] = {0, 0, 0};  // FP32 multi-RHS stencil ms per RHS at 4 RHS: kernels 1, 2, 3
+    float tune_mrhs_ms[6] = {0, 0, 0, 0, 0, 0};   // FP32 multi-RHS stencil ms per RHS of kernels 1, 2, 3
+                                                    // at 4 right-hand sides, then at 12
     int sap_tps = 1;                   // threads per site of the FP32 Schwarz block kernel
     double t_sign64 = 0, t_sign_low = 0, t_prec = 0;   // phase wall times of the current solve (s)
     bool sap_tuned = false;

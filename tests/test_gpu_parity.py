@@ -438,9 +438,10 @@ def test_autotuner_reports_a_choice():
     t = op.tuning()
     assert t["tps64"] in (1, 4) and t["tps32"] in (1, 4)
     assert all(m > 0 for m in t["ms"])
-    t = op.tuning_mrhs()   # multi-RHS kernel: the fastest of the three timed per right-hand side
-    assert t["kernel"] in (1, 2, 3) and all(m > 0 for m in t["ms"])
-    assert t["ms"][t["kernel"] - 1] == min(t["ms"])
+    t = op.tuning_mrhs()   # multi-RHS kernels: the fastest of the three per right-hand side, at 4 and 12
+    assert t["kernel"] in (1, 2, 3) and t["kernel_large"] in (1, 2, 3)
+    assert all(m > 0 for m in t["ms4"] + t["ms12"])
+    assert t["ms4"][t["kernel"] - 1] == min(t["ms4"]) and t["ms12"][t["kernel_large"] - 1] == min(t["ms12"])
     op.close()
     with pytest.raises(ovl.OvlError) as e:
         ovl.Overlap(U, dims, 1.0, 0.01, params(mrhs_kernel=4))

@@ -94,7 +94,8 @@ def test_wilson_multi_rhs_fp32_matches_oracle(nrhs, kernel):
     psi = np.stack([synth.rhs_gaussian(dims, 1400 + k) for k in range(nrhs)])
     p = ovl.params_default(lambda_min=0.05, lambda_max=8.0, mrhs_kernel=kernel)
     op = ovl.Overlap(U, dims, 1.0, 0.05, p)
-    assert op.tuning_mrhs()["kernel"] == kernel
+    t = op.tuning_mrhs()
+    assert t["kernel"] == kernel and t["kernel_large"] == kernel
     out = torch.empty_like(dev(psi))
     op.wilson_apply_n_arith(out, dev(psi), nrhs, -0.7, ovl.OVL_ARITH_FP32)
     o = host(out)
