@@ -456,7 +456,9 @@ def test_autotuner_reports_a_choice():
 def test_config4_half_storage_full_size():
     """32^3 x 64, 3-stout links, mu = 0.01, one Z2 source: FP16-stored inner multishift,
     FP64 outer FGMRES, tol 1e-10. The oracle cannot solve at this size; the check is the
-    true residual through the FP64 D_N (itself pinned to the oracle at smaller volumes)."""
+    true residual through the FP64 D_N (itself pinned to the oracle at smaller volumes), and
+    that D_N's stencil on the solution against the oracle's definitional stencil on the whole
+    lattice."""
     dims = (64, 32, 32, 32)
     U = torch.from_numpy(synth.gauge_field(dims, 0.5, 1004, stout_steps=3, device="cuda")).cuda()
     b = torch.from_numpy(synth.rhs_z2(dims, 2004)).cuda()
@@ -469,6 +471,11 @@ def test_config4_half_storage_full_size():
     res = ((b - r).norm() / b.norm()).item()
     assert res < 2e-10, (res, stats)
     assert stats["ms_iters_low"] > 0
+    w = torch.empty_like(x)
+    op.wilson_apply(w, x, -1.0)
+    ref = sparse.wilson(x.cpu().numpy(), U.cpu().numpy(), dims, -1.0)
+    err = np.abs(w.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < 1e-12, err
     op.close()
 
 
