@@ -4,7 +4,7 @@ relaxation factor of the sign accuracy (Sec. 5.2, Table 2 uses 1e-2).
 
     python -m paper_1410_7170_gb300.scan [--lattice 16x16x16x16] [--mu 0.01]
         [--m0 -0.6:0.0:0.05] [--relax 0.01,0.03,0.1,0.3] [--adapt] [--reps 3]
-        [--set eps_inner=0.01,0.03 --set sap_mr_iters=4,6 ...]
+        [--set eps_inner=0.01,0.03 --set sap_mr_iters=4,6 --set sap_block=4x4x4x4,4x4x4x2 ...]
 
 Each point is a full solve (outer FP64 FGMRES, recursive inner FP32 FGMRES, Wilson
 preconditioner) of the seeded workload (links exp(i 0.5 H) smeared by 3 stout steps, one
@@ -57,7 +57,8 @@ def main(argv=None):
     grid = [{}]
     for spec in a.set:
         key, vals = spec.split("=", 1)
-        parsed = [int(v) if v.lstrip("-").isdigit() else float(v) for v in vals.split(",")]
+        parsed = [tuple(int(u) for u in v.split("x")) if "x" in v else int(v) if v.lstrip("-").isdigit()
+                  else float(v) for v in vals.split(",")]   # "4x4x4x2" for the array fields
         grid = [dict(g, **{key: v}) for g in grid for v in parsed]
     build.build()
     dims = tuple(int(v) for v in a.lattice.split("x"))
