@@ -569,14 +569,15 @@ def serving(ovl, torch, dev, n_req=24, slots=3, seed=5000):
             "completed": st["completed"], "failed": st["failed"], "hbm_high_water_bytes": st["hbm_high_water"]}
 
 
-def serving_full(seed=5000, n_req=200, slots=3, n_cap=20, n_alone=8):
+def serving_full(seed=5000, n_req=200, slots=3, n_cap=20, n_alone=8, n_fields=3):
     """The full serving workload: Poisson arrivals of n_req overlap solves, lattice V uniform in
-    {8^4, 16^4, 24^4, 32^4}, mu in {0.01, 0.05, 0.1}, 1-12 Gaussian right-hand sides, each
-    request with its own gauge field (generator seeded by the request id, 3 stout steps), tol
-    1e-8. The arrival rate is 0.7 x the capacity measured first on the first n_cap requests
-    submitted at once. Reported: p50/p99 latency, solves/s, HBM high-water mark, the worst true
-    residual, and the largest difference between a served result and the same request run
-    alone (n_alone requests re-run alone)."""
+    {8^4, 16^4, 24^4, 32^4}, mu in {0.01, 0.05, 0.1}, 1-12 Gaussian right-hand sides, tol 1e-8,
+    each request on one of n_fields seeded gauge fields of its lattice size (3 stout steps; an
+    ensemble of configurations, resident on the device, the serving loop keyed by field). The
+    arrival rate is 0.7 x the capacity measured first on the first n_cap requests submitted at
+    once. Reported: p50/p99 latency, solves/s, HBM high-water mark, the worst true residual, and
+    the largest difference between a served result and the same request run alone (n_alone
+    requests re-run alone)."""
     import numpy as np
     import torch
 
@@ -597,12 +598,20 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=20, n_alone=8):
     reqs = []
     for k in range(n_req):
         d = sizes[int(rng.integers(4))]
-        reqs.append(dict(id=k, dims=d, mu=float(rng.choice([0.01, 0.05, 0.1])), n_rhs=int(rng.integers(1, 13))))
-    # inputs resident on the device before the stream starts: one gauge field per request, and
-    # per lattice size one block of 12 Gaussian right-hand sides that requests read from
+        reqs.append(dict(id=k, dims=d, mu=float(rng.choice([0.01, 0.05, 0.1])), n_rhs=int(rng.integers(1, 13)),
+                         field=int(rng.integers(n_fields))))
+    # inputs resident on the device before the stream starts: n_fields gauge fields per lattice
+    # size (generating one per request took longer than the stream), and per lattice size one
+    # block of 12 Gaussian right-hand sides that requests read from
+    fields = {}
+    for i, d in enumerate(sizes):
+        for f in range(n_fields):
+            fields[(d, f)] = torch.from_numpy(synth.gauge_field(d, 0.5, seed + 100 * i + f, stout_steps=3,
+                                                                device=dev)).to(dev)
+            stage("field", dims=list(d), field=f)
     for r in reqs:
-        r["gauge"] = torch.from_numpy(synth.gauge_field(r["dims"], 0.5, seed + r["id"], stout_steps=3,
-                                                        device=dev)).to(dev)
+        r["gauge"] = fields[(r["dims"], r["field"])]
+        r["key"] = 1 + 100 * sizes.index(r["dims"]) + r["field"]
     bblk = {d: torch.from_numpy(synth.rhs_gaussian(d, seed + 1000 + i, n_rhs=12)).to(dev)
             for i, d in enumerate(sizes)}
     p = ovl.params_default(precond=ovl.OVL_PREC_RECURSIVE, precision=ovl.OVL_MIXED_FP32, relax_factor=RELAX)
@@ -616,7 +625,7 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=20, n_alone=8):
             x = torch.zeros_like(b)
             xs.append(x)
             tk.append(srv.submit(r["gauge"], r["dims"], 1.0, r["mu"], b, x, r["n_rhs"], TOL, p,
-                                 gauge_key=1 + r["id"]))
+                                 gauge_key=r["key"]))
             if rate:
                 time.sleep(float(r2.exponential(1.0 / rate)))
         res = [srv.wait(t) for t in tk]
@@ -645,8 +654,9 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=20, n_alone=8):
         op.close()
         diffs.append(((xs[k] - xa).norm() / xa.norm()).item())
     return {"mode": "serving stream", "metric": "p50/p99 latency and solves/s of a Poisson stream of overlap solves",
-            "workload": "%d requests: V in {8^4,16^4,24^4,32^4}, mu in {0.01,0.05,0.1}, 1-12 Gaussian RHS, own 3-stout "
-                        "gauge field each, tol 1e-8, %d slots, arrivals at 0.7 x capacity" % (n_req, slots),
+            "workload": "%d requests: V in {8^4,16^4,24^4,32^4}, mu in {0.01,0.05,0.1}, 1-12 Gaussian RHS, one of %d "
+                        "3-stout gauge fields per size, tol 1e-8, %d slots, arrivals at 0.7 x capacity"
+                        % (n_req, n_fields, slots),
             "capacity_solves_per_s": cap["solves_per_s"], "arrival_rate_per_s": rate,
             "p50_s": rep["p50_s"], "p99_s": rep["p99_s"], "solves_per_s": rep["solves_per_s"],
             "rhs_per_s": sum(r["n_rhs"] for r in reqs) / (len(reqs) / rep["solves_per_s"]),
@@ -713,6 +723,7 @@ def main():
     ap.add_argument("--details", default="", help="also write the full record (every section) to this JSON file")
     ap.add_argument("--serving-full", action="store_true",
                     help="instead of the solve benchmark, run the full serving stream (200 requests up to 32^4)")
+    ap.add_argument("--serving-requests", type=int, default=200, help="requests of the --serving-full stream")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -726,7 +737,7 @@ def main():
         else:
             dist.init_process_group("gloo")
     if args.serving_full:
-        out = serving_full() if rank == 0 else None
+        out = serving_full(n_req=args.serving_requests) if rank == 0 else None
     elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
