@@ -569,7 +569,7 @@ def serving(ovl, torch, dev, n_req=24, slots=3, seed=5000):
             "completed": st["completed"], "failed": st["failed"], "hbm_high_water_bytes": st["hbm_high_water"]}
 
 
-def serving_full(seed=5000, n_req=200, slots=3, n_cap=20, n_alone=8, n_fields=3):
+def serving_full(seed=5000, n_req=200, slots=3, n_cap=None, n_alone=None, n_fields=3):
     """The full serving workload: Poisson arrivals of n_req overlap solves, lattice V uniform in
     {8^4, 16^4, 24^4, 32^4}, mu in {0.01, 0.05, 0.1}, 1-12 Gaussian right-hand sides, tol 1e-8,
     each request on one of n_fields seeded gauge fields of its lattice size (3 stout steps; an
@@ -587,6 +587,8 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=20, n_alone=8, n_fields=3)
 
     build.build()
     t_start = time.perf_counter()
+    n_cap = n_cap or max(4, min(20, n_req // 4))      # capacity probe: a quarter of the stream, at most 20
+    n_alone = n_alone or max(2, min(8, n_req // 10))  # requests re-run alone
 
     def stage(msg, **kw):   # progress on stderr, so a cut-short run still tells how far it got
         print(json.dumps({"stage": msg, "t_s": round(time.perf_counter() - t_start, 1), **kw}), file=sys.stderr,
