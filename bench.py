@@ -643,10 +643,12 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=None, n_alone=None, n_fiel
     stage("capacity measured", solves_per_s=cap["solves_per_s"])
     rep, res, xs = run(reqs, rate)
     stage("stream done", p50_s=rep["p50_s"], p99_s=rep["p99_s"], solves_per_s=rep["solves_per_s"])
-    worst_res = max(x["stats"]["true_rel_resid"] for x in res)
+    failures = [{"id": r["id"], "dims": list(r["dims"]), "n_rhs": r["n_rhs"], "status": x["status"],
+                 "message": x["message"]} for r, x in zip(reqs, res) if x["status"] != 0]
+    worst_res = max(x["stats"]["true_rel_resid"] for x in res if x["status"] == 0)
     # a sample of requests re-run alone: the served result must be the same, bit for bit
     diffs = []
-    pick = [r for r in reqs if r["n_rhs"] > 1][:n_alone]
+    pick = [r for r, x in zip(reqs, res) if r["n_rhs"] > 1 and x["status"] == 0][:n_alone]
     for r in pick:
         k = reqs.index(r)
         b = bblk[r["dims"]][:r["n_rhs"]]
@@ -664,7 +666,7 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=None, n_alone=None, n_fiel
             "rhs_per_s": sum(r["n_rhs"] for r in reqs) / (len(reqs) / rep["solves_per_s"]),
             "completed": rep["completed"], "failed": rep["failed"], "hbm_high_water_bytes": rep["hbm_high_water"],
             "worst_true_rel_resid": worst_res, "mix_vs_alone_max_rel_diff": max(diffs) if diffs else None,
-            "alone_sample": len(diffs)}
+            "alone_sample": len(diffs), "failures": failures}
 
 
 def cpu_baseline(budget_s=30.0):

@@ -122,6 +122,15 @@ size_t estimate_bytes(const ovl_request &r, const ovl_params &p) {
     return (size_t)(b * 1.1) + ((size_t)64 << 20);
 }
 
+// Frees every idle cached context. Called with the lock held.
+void evict_idle(ovl_server *s) {
+    for (auto &cc : s->idle) {
+        s->cached -= cc.bytes;
+        ovl_destroy(cc.ctx);
+    }
+    s->idle.clear();
+}
+
 void run_job(ovl_server *s, Job *j) {
     // context: the cached one claimed at admission, or a new one
     ovl_ctx *ctx = j->claimed;
@@ -133,6 +142,22 @@ void run_job(ovl_server *s, Job *j) {
     ovl_stats stats;
     memset(&stats, 0, sizeof(stats));
     if (st == OVL_OK) st = ovl_solve(ctx, j->req.x, j->req.b, j->req.n_rhs, j->req.tol, &stats);
+    if (st == OVL_ENOMEM) {
+        // the device ran out although the estimates fitted the budget (a running request using
+        // more than its estimate): free every idle resident context and try once more from a new
+        // context (the solve starts again from whatever x holds)
+        if (ctx) {
+            ovl_destroy(ctx);
+            ctx = nullptr;
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            evict_idle(s);
+        }
+        st = ovl_create(&ctx, j->req.gauge, j->req.dims, j->req.rho, j->req.mu, &j->params, nullptr);
+        if (ctx) reinterpret_cast<ovl::Ctx *>(ctx)->fixed_batch = true;
+        if (st == OVL_OK) st = ovl_solve(ctx, j->req.x, j->req.b, j->req.n_rhs, j->req.tol, &stats);
+    }
     if (st != OVL_OK && ctx) {
         strncpy(j->res.message, ovl_last_error(ctx), sizeof(j->res.message) - 1);
     } else if (st != OVL_OK) {
