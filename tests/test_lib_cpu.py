@@ -1,7 +1,9 @@
 """Host-only checks of the C-ABI library: it builds, loads without a GPU,
-exports every function include/ovl.h declares, and its host-side Zolotarev
+exports every function include/ovl.h declares, its Python struct mirrors match the C layout,
+and its host-side Zolotarev
 coefficients (own AGM/Landen elliptic functions) match the oracle's
 (scipy elliptic functions, grid-centred scale)."""
+import ctypes
 import os
 import re
 import subprocess
@@ -148,3 +150,28 @@ def test_request_bytes_estimate_covers_options():
     assert ovl.request_bytes(dims, n_rhs=4) > base
     with pytest.raises(ovl.OvlError):
         ovl.request_bytes((0, 4, 4, 4))
+
+
+def test_binding_structs_match_the_c_abi(tmp_path):
+    """Every ctypes mirror of an ovl.h struct has the C struct's size and each field the C
+    offset (compiled from include/ovl.h with the host C compiler): a field added on one side
+    only would otherwise shift every later field silently."""
+    mirrors = [ovl.ovl_params, ovl.ovl_stats, ovl.ovl_request, ovl.ovl_result, ovl.ovl_prof_kernel, ovl.ovl_prof]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ovl.h"', "int main(void) {"]
+    for m in mirrors:
+        name = m.__name__
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in m._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for m in mirrors:
+        name = m.__name__
+        assert int(got[name]) == ctypes.sizeof(m), name
+        for f in m._fields_:
+            assert int(got["%s.%s" % (name, f[0])]) == getattr(m, f[0]).offset, (name, f[0])
