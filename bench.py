@@ -5,10 +5,11 @@ workload: seeded near-identity SU(3) links (eps = 0.5) smeared by 3 stout steps
 (rho_stout = 0.1), rho = 1, mu = 0.01, one Gaussian right-hand side. The headline
 arm is the mixed-precision solver (outer FP64 FGMRES, recursive inner FP32
 FGMRES with an FP32 sign function, inexact FP32 Wilson preconditioner at
-m0^def); the plain FP64 arm (FP64 everywhere, Wilson-preconditioned FGMRES) is
-timed beside it. The mixed arm's FP64-accuracy sign applications run in float-float
-arithmetic on the FP32 pipes (params.ff_outer). Multi-GPU: replicas only (one
-independent solve per rank).
+m0_prec = 0, the best point of the paper's scan range on this workload); the plain
+FP64 arm (FP64 everywhere, Wilson-preconditioned FGMRES) is timed beside it. The
+mixed arm's FP64-accuracy sign applications run in float-float arithmetic on the
+FP32 pipes (params.ff_outer). Multi-GPU: replicas only (one independent solve per
+rank).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
