@@ -670,6 +670,9 @@ def serving_full(seed=5000, n_req=200, slots=3, n_cap=None, n_alone=None, n_fiel
             "alone_sample": len(diffs), "failures": failures}
 
 
+_ORACLE_CACHE = {}
+
+
 def cpu_baseline(budget_s=30.0):
     """The oracle as it stands on the host cores: one D_N application at the workload size
     (the definitional stencil and one plain FP64 CG per Zolotarev pole, 20 poles on the
@@ -679,8 +682,10 @@ def cpu_baseline(budget_s=30.0):
     import numpy as np
     from oracle import dense, sparse, zolotarev
     import synth
-    U = synth.gauge_field(DIMS, 0.5, GAUGE_SEED, stout_steps=3, stout_eps=0.1)
-    b = synth.rhs_gaussian(DIMS, RHS_SEED)
+    if "inputs" not in _ORACLE_CACHE:   # the workload's inputs, drawn once per process
+        _ORACLE_CACHE["inputs"] = (synth.gauge_field(DIMS, 0.5, GAUGE_SEED, stout_steps=3, stout_eps=0.1),
+                                   synth.rhs_gaussian(DIMS, RHS_SEED))
+    U, b = _ORACLE_CACHE["inputs"]
     lmin, lmax = ORACLE_INTERVAL
     co = zolotarev.zolotarev_coefficients(lmin / lmax, 20)
     rho = dense.rho_from_mu(0.01, -1.0)
