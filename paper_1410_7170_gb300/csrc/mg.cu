@@ -56,11 +56,6 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // out[B * ob + off + chi * nv + k] = <P_k restricted to aggregate (B, chi), r>: one CTA per
 // (block B, test vector k), one thread per block site, one block-wide sum of two complex numbers.
