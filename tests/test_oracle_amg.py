@@ -20,7 +20,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import amg, dense, gamma
+from oracle import amg, gamma
 
 
 @pytest.fixture(scope="module")

@@ -6,7 +6,6 @@ boundary phase) breaks at least one of them.
 """
 import numpy as np
 import pytest
-import scipy.sparse as sp
 
 import synth
 from oracle import dense, freefield, observables
